@@ -1,0 +1,255 @@
+"""FP64 CPU oracle for Min-Path-Tracing.  TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library and its Python
+binding never touch it.  The arithmetic lives in ``mpt_oracle.cpp`` (plain
+FP64 C++, see its header for the paper passages each part follows); this
+module only compiles it with g++ and marshals numpy arrays.
+
+Parity unpinned: completeness of the multi-root solution sets of curved
+sequences of order >= 2 (multi-start agreement only).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mpt_oracle.cpp")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+TAU = 1e-20  # acceptance threshold on the normalised cost (Algorithm 1)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with g++ (host code only)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC, "-lpthread"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Scene(C.Structure):
+    _fields_ = [
+        ("n_obj", C.c_int32), ("obj_kind", C.c_void_p), ("obj_param", C.c_void_p),
+        ("n_occ", C.c_int32), ("occ_kind", C.c_void_p), ("occ_param", C.c_void_p),
+        ("scale", C.c_double), ("tx", C.c_void_p), ("n_tx", C.c_int32),
+        ("rx", C.c_void_p), ("n_rx", C.c_int32), ("pair_mode", C.c_int32),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            P, I32, I64, U64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+            L.oracle_enumerate.restype = I64
+            L.oracle_enumerate.argtypes = [I32, P, I32, P, U64, I32, I32, P, P, P, P, I64]
+            L.oracle_solve.restype = C.c_int
+            L.oracle_solve.argtypes = [P, I64, P, P, P, I64, I64, I64, U64, P, P, P, P, P, C.c_int]
+            L.oracle_validate.restype = C.c_int
+            L.oracle_validate.argtypes = [P, I64, P, P, I64, I64, I64, P, P, P, D, P, P, P, C.c_int]
+            L.oracle_path_grad.restype = C.c_int
+            L.oracle_path_grad.argtypes = [P, I32, P, P, P, P, P, P]
+            L.oracle_residual.restype = C.c_int
+            L.oracle_residual.argtypes = [P, I32, P, P, P, P, P, P]
+            L.oracle_segment_blocked.restype = C.c_int
+            L.oracle_segment_blocked.argtypes = [P, P, P, P]
+            L.oracle_params_in_bounds.restype = C.c_int
+            L.oracle_params_in_bounds.argtypes = [P, I32, P, P]
+            L.oracle_abi_version.restype = C.c_int
+            L.oracle_splitmix64.restype = U64
+            L.oracle_splitmix64.argtypes = [U64]
+            L.oracle_threads.restype = C.c_int
+            L.oracle_threads.argtypes = [C.c_int]
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class SceneRef:
+    """Keeps the numpy arrays alive while the C struct points at them."""
+
+    def __init__(self, scene):
+        self.scene = scene.contiguous()
+        s = self.scene
+        self.struct = _Scene(s.n_obj, _p(s.obj_kind).value, _p(s.obj_param).value, s.n_occ,
+                             _p(s.occ_kind).value, _p(s.occ_param).value, s.scale, _p(s.tx).value,
+                             s.tx.shape[0], _p(s.rx).value, s.rx.shape[0], s.pair_mode)
+
+    @property
+    def ptr(self):
+        return C.cast(C.pointer(self.struct), C.c_void_p)
+
+
+@dataclasses.dataclass
+class SequenceTable:
+    order: np.ndarray  # int32 [E]
+    ids: np.ndarray  # int32 [E, 4] (-1 padded)
+    start: np.ndarray  # int32 [E]
+
+    def __len__(self):
+        return int(self.order.shape[0])
+
+
+def enumerate_sequences(scene, max_order: int, spec, adj: np.ndarray | None = None) -> SequenceTable:
+    """Sequence table of Algorithm 1 (all_simple_paths / seeded quotas)."""
+    L = lib()
+    kinds = np.ascontiguousarray(scene.obj_kind, np.int32)
+    quota = np.ascontiguousarray(spec.as_array(), np.int64)
+    adj_p = None
+    if adj is not None:
+        adj = np.ascontiguousarray(adj, np.uint8)
+        adj_p = _p(adj)
+    args = (scene.n_obj, _p(kinds), max_order, _p(quota), spec.seed, spec.starts_curved,
+            spec.force_edges_every, adj_p)
+    e = np.zeros(1, np.int32)
+    n = L.oracle_enumerate(*args, _p(e), _p(np.zeros(4, np.int32)), _p(e), 0)
+    order = np.zeros(n, np.int32)
+    ids = np.zeros((n, 4), np.int32)
+    start = np.zeros(n, np.int32)
+    n2 = L.oracle_enumerate(*args, _p(order), _p(ids), _p(start), n)
+    assert n2 == n
+    return SequenceTable(order, ids, start)
+
+
+@dataclasses.dataclass
+class Solutions:
+    X: np.ndarray  # float64 [n, 12] interaction points
+    T: np.ndarray  # float64 [n, 8] object parameters (Eqs. 13-14)
+    cost: np.ndarray  # float64 [n]
+    status: np.ndarray  # int32 [n]
+    iters: np.ndarray  # int32 [n]
+    begin: int = 0
+
+
+def solve(scene, table: SequenceTable, begin: int = 0, end: int | None = None, init_seed: int = 0,
+          threads: int = 0) -> Solutions:
+    """Levenberg-Marquardt solve of candidates [begin, end) (c = entry * n_pairs + pair)."""
+    L = lib()
+    ref = SceneRef(scene)
+    n_pairs = scene.n_pairs
+    total = len(table) * n_pairs
+    end = total if end is None else min(end, total)
+    n = max(end - begin, 0)
+    X = np.zeros((n, 12), np.float64)
+    T = np.zeros((n, 8), np.float64)
+    cost = np.zeros(n, np.float64)
+    status = np.zeros(n, np.int32)
+    iters = np.zeros(n, np.int32)
+    if n:
+        L.oracle_solve(ref.ptr, len(table), _p(table.order), _p(table.ids), _p(table.start), n_pairs,
+                       begin, end, init_seed, _p(X), _p(T), _p(cost), _p(status), _p(iters), threads)
+    return Solutions(X, T, cost, status, iters, begin)
+
+
+@dataclasses.dataclass
+class Verdicts:
+    valid: np.ndarray  # int32 [n]
+    ambiguous: np.ndarray  # int32 [n]
+    length: np.ndarray  # float64 [n]
+
+
+def validate(scene, table: SequenceTable, sol: Solutions, tau: float = TAU, threads: int = 0) -> Verdicts:
+    L = lib()
+    ref = SceneRef(scene)
+    n = sol.X.shape[0]
+    valid = np.zeros(n, np.int32)
+    amb = np.zeros(n, np.int32)
+    length = np.zeros(n, np.float64)
+    if n:
+        X = np.ascontiguousarray(sol.X)
+        T = np.ascontiguousarray(sol.T)
+        cost = np.ascontiguousarray(sol.cost)
+        L.oracle_validate(ref.ptr, len(table), _p(table.order), _p(table.ids), scene.n_pairs, sol.begin,
+                          sol.begin + n, _p(X), _p(T), _p(cost), tau, _p(valid), _p(amb), _p(length),
+                          threads)
+    return Verdicts(valid, amb, length)
+
+
+def candidate_range(scene, table: SequenceTable, begin: int, end: int, init_seed: int = 0,
+                    threads: int = 0):
+    sol = solve(scene, table, begin, end, init_seed, threads)
+    ver = validate(scene, table, sol, threads=threads)
+    return sol, ver
+
+
+def _n_params(scene, ids):
+    return sum(1 if scene.obj_kind[i] in (2, 3) else 2 for i in ids)
+
+
+def path_grad(scene, ids, a, b, T):
+    """dL/dtheta (theta = TX[3], RX[3], plane offsets d_k) and dX/dtheta at
+    a converged path with parameters T."""
+    L = lib()
+    ref = SceneRef(scene)
+    ids = np.asarray([i for i in ids if i >= 0], np.int32)
+    n = len(ids)
+    a = np.ascontiguousarray(a, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    T = np.ascontiguousarray(np.asarray(T, np.float64).reshape(-1)[:_n_params(scene, ids)])
+    dL = np.zeros(6 + n, np.float64)
+    dX = np.zeros((3 * n, 6 + n), np.float64)
+    rc = L.oracle_path_grad(ref.ptr, n, _p(ids), _p(a), _p(b), _p(T), _p(dL), _p(dX))
+    if rc != 0:
+        raise RuntimeError("oracle_path_grad: singular normal matrix")
+    return dL, dX
+
+
+def residual(scene, ids, a, b, T):
+    """Stacked law residual (Eq. 10) and the points X(T)."""
+    L = lib()
+    ref = SceneRef(scene)
+    ids = np.asarray([i for i in ids if i >= 0], np.int32)
+    n = len(ids)
+    out = np.zeros(12, np.float64)
+    X = np.zeros(3 * n, np.float64)
+    T = np.ascontiguousarray(np.asarray(T, np.float64).reshape(-1)[:_n_params(scene, ids)])
+    m = L.oracle_residual(ref.ptr, n, _p(ids), _p(np.ascontiguousarray(a, np.float64)),
+                          _p(np.ascontiguousarray(b, np.float64)), _p(T), _p(out), _p(X))
+    return out[:m], X
+
+
+def cost(scene, ids, a, b, T) -> float:
+    return float(np.sum(residual(scene, ids, a, b, T)[0] ** 2))
+
+
+def segment_blocked(scene, A, B) -> tuple[bool, bool]:
+    L = lib()
+    ref = SceneRef(scene)
+    amb = np.zeros(1, np.int32)
+    r = L.oracle_segment_blocked(ref.ptr, _p(np.ascontiguousarray(A, np.float64)),
+                                 _p(np.ascontiguousarray(B, np.float64)), _p(amb))
+    return bool(r), bool(amb[0])
+
+
+def params_in_bounds(scene, obj, u) -> tuple[bool, bool]:
+    L = lib()
+    ref = SceneRef(scene)
+    amb = np.zeros(1, np.int32)
+    u = np.ascontiguousarray(np.asarray(u, np.float64).reshape(-1))
+    r = L.oracle_params_in_bounds(ref.ptr, int(obj), _p(u), _p(amb))
+    return bool(r), bool(amb[0])
+
+
+def splitmix64(x: int) -> int:
+    return int(lib().oracle_splitmix64(x & 0xFFFFFFFFFFFFFFFF))
+
+
+def threads(n: int = 0) -> int:
+    return int(lib().oracle_threads(n))
