@@ -1,0 +1,288 @@
+/* Min-Path-Tracing (MPT) on one GPU: C ABI.
+ *
+ * The calls follow the problem statement of Algorithm 1 of the paper
+ * (Eertmans, Oestges, Jacques, "Min-Path-Tracing: A Diffraction Aware
+ * Alternative to Image Method in Ray Tracing", arXiv 2301.06399): inputs are
+ * the maximum number of interactions n_t, the objects database D and the
+ * BS / UE positions; the output is the set S of valid paths.
+ *
+ *   mpt_scene_upload  objects database D (Sec. II: implicit surfaces and
+ *                     edges with their bounds; occluders)
+ *   mpt_enumerate     path candidates (Algorithm 1, all_simple_paths; Sec. III)
+ *   mpt_solve         find_minimum_path for every candidate (Algorithm 1;
+ *                     Eqs. 8, 9, 13-15)
+ *   mpt_validate      "C < threshold and X is valid" (Algorithm 1) and the
+ *                     union into S, as a compacted list
+ *   mpt_grad          gradients of path length / points at converged paths
+ *                     (implicit-function theorem on Eq. 15; not in the paper)
+ *
+ * Conventions
+ *   - Every call returns an int status (MPT_OK = 0); no exception crosses the
+ *     ABI.  mpt_status_string() names a status.
+ *   - Device buffers are allocated and owned by the caller; the library never
+ *     frees them.  Opaque handles (mpt_ctx, mpt_scene) are owned by the
+ *     library and released with their destroy/free call.
+ *   - Work is enqueued asynchronously on the caller's CUDA stream (passed as
+ *     void*, a cudaStream_t; NULL = legacy default stream).  Counts are written
+ *     to device memory; no call synchronises the stream unless it says so.
+ *   - Arguments are checked on the host before anything is enqueued; a bad
+ *     argument returns MPT_ERR_ARG and enqueues nothing.  A CUDA launch or
+ *     allocation failure returns MPT_ERR_CUDA.
+ *   - One mpt_ctx per device and thread of control: calls that share a ctx
+ *     must be issued from one host thread at a time.
+ */
+#ifndef MPT_H_
+#define MPT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MPT_OK = 0,
+  MPT_ERR_ARG = 1,         /* invalid argument (null pointer, size, kind) */
+  MPT_ERR_CUDA = 2,        /* CUDA runtime error (launch, allocation, copy) */
+  MPT_ERR_CAPACITY = 3,    /* an output buffer is too small (see each call) */
+  MPT_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+  MPT_ERR_UNSUPPORTED = 5  /* valid request this build does not support */
+};
+
+/* Object kinds (Sec. II).  Parameter records are double[24]:
+ *   MPT_PLANE       [0:3] unit normal n, [3] d with <n,X> = d, [4:7] corner O,
+ *                   [7:10] unit axis U_ax, [10:13] unit axis V_ax (n = U_ax x V_ax),
+ *                   [13] U, [14] V: the facet is O + s U_ax + t V_ax, s in [0,U],
+ *                   t in [0,V]
+ *   MPT_PARABOLOID  [0:9] rotation R (row-major, columns = local axes in world),
+ *                   [9:12] apex t0, [12] focal length f, [13] disc radius rho:
+ *                   X = t0 + R (s, t, (s^2+t^2)/(4f)), s^2 + t^2 <= rho^2
+ *   MPT_LINE_EDGE   [0:3] point P, [3:6] unit direction e, [6] t0, [7] t1:
+ *                   X = P + t e, t in [t0, t1]
+ *   MPT_ARC_EDGE    [0:3] centre C, [3:6] unit axis a, [6] radius Rc,
+ *                   [7:10] unit reference u (orthogonal to a), [10] phi0,
+ *                   [11] phi1: X = C + Rc (cos t u + sin t (a x u)),
+ *                   t in [phi0, phi1] modulo 2 pi
+ * Occluder kinds (surfaces a segment may not cross; edges never occlude):
+ *   MPT_OCC_RECT       [0:3] O, [3:6] U_ax, [6:9] V_ax, [9] U, [10] V, [11:14] n
+ *   MPT_OCC_PARABOLOID same record as MPT_PARABOLOID
+ */
+enum { MPT_PLANE = 0, MPT_PARABOLOID = 1, MPT_LINE_EDGE = 2, MPT_ARC_EDGE = 3 };
+enum { MPT_OCC_RECT = 0, MPT_OCC_PARABOLOID = 1 };
+#define MPT_RECORD 24
+#define MPT_MAX_ORDER 4
+#define MPT_MAX_OBJECTS 65535
+#define MPT_MAX_OCCLUDERS 1024
+
+/* Solver precision modes. */
+enum {
+  MPT_FP64_PLAIN = 0,       /* FP64 throughout (the plain GPU method) */
+  MPT_FP32 = 1,             /* FP32 iterations only, no refinement */
+  MPT_FP32_FP64REFINE = 2   /* FP32 iterations, FP64 refinement of candidates
+                               that pass the FP32 cost/bounds prescreen */
+};
+
+/* Per-candidate termination status (low 4 bits) and flags. */
+enum {
+  MPT_PATH_CONVERGED = 0,   /* step or cost below tolerance */
+  MPT_PATH_MAXITER = 1,     /* iteration cap reached */
+  MPT_PATH_DIVERGED = 2,    /* a point left the cube of half-side 1e3 S */
+  MPT_PATH_STALLED = 3,     /* line search could not decrease the cost */
+  MPT_PATH_NONFINITE = 4,   /* NaN / Inf in the cost */
+  MPT_PATH_REFINED = 0x10,  /* flag: FP64 refinement ran; cost is FP64 */
+  MPT_PATH_PRESCREENED = 0x20 /* flag: FP32 prescreen rejected (no refinement) */
+};
+
+typedef struct mpt_ctx mpt_ctx;
+typedef struct mpt_scene mpt_scene;
+
+/* Host description of a scene (copied by mpt_scene_upload; the caller keeps
+ * ownership of these arrays). */
+typedef struct {
+  int32_t n_obj;
+  const int32_t* obj_kind;   /* host [n_obj] */
+  const double* obj_param;   /* host [n_obj][MPT_RECORD] */
+  int32_t n_occ;
+  const int32_t* occ_kind;   /* host [n_occ] */
+  const double* occ_param;   /* host [n_occ][MPT_RECORD] */
+  double scale;              /* scene scale S in metres (> 0) */
+} mpt_scene_desc;
+
+/* TX / RX endpoints (device, caller-owned, read by solve/validate/grad). */
+typedef struct {
+  const double* tx;   /* device [n_tx][3] */
+  int32_t n_tx;
+  const double* rx;   /* device [n_rx][3] */
+  int32_t n_rx;
+  int32_t pair_mode;  /* 0: pair p = t * n_rx + r (all combinations);
+                         1: pair p uses tx[p] and rx[p] (n_tx == n_rx) */
+} mpt_endpoints;
+
+/* Which sequences to enumerate.  quota[n-1] for order n: -1 = every ordered
+ * sequence of n distinct objects (lexicographic order of the ids), 0 = none,
+ * q > 0 = q sequences drawn with SplitMix64 from `seed` (slot rule in the
+ * design notes).  Sequences containing a paraboloid or an arc are repeated
+ * `starts_curved` times with start index 0..starts_curved-1.  For orders
+ * >= 3, every `force_edges_every`-th drawn slot places two consecutive edges
+ * (0 = never). */
+typedef struct {
+  int64_t quota[MPT_MAX_ORDER];
+  uint64_t seed;
+  int32_t starts_curved;
+  int32_t force_edges_every;
+} mpt_sampling;
+
+/* Candidate list (caller-owned device buffers).  Entry e of the sequence
+ * table and pair p give candidate c = e * n_pairs + p (pairs fastest, so a
+ * warp shares one object sequence).  rec[c] is 16 bytes:
+ *   rec[c].x = pair index p
+ *   rec[c].y = id0 | id1 << 16   (0xFFFF = unused slot)
+ *   rec[c].z = id2 | id3 << 16
+ *   rec[c].w = order | start << 8
+ * order_begin (device int64[5]) = [first candidate of order 1, of order 2,
+ * of order 3, of order 4, end]; the number of candidates is order_begin[4]
+ * (also written to *count). */
+typedef struct {
+  uint32_t* rec;         /* device [capacity][4] */
+  int64_t capacity;      /* entries rec can hold */
+  int64_t* count;        /* device int64[1]: number of candidates */
+  int64_t* order_begin;  /* device int64[5] */
+  uint64_t init_seed;    /* seed of the initial guesses of starts > 0 */
+} mpt_candidates;
+
+/* Per-candidate solver output (caller-owned device SoA, capacity >= count). */
+typedef struct {
+  double* T;         /* device [8][capacity]: parameters, slot j of candidate c at T[j*capacity + c] */
+  double* cost;      /* device [capacity]: cost of Eq. 15 (FP64 after refinement) */
+  uint8_t* status;   /* device [capacity]: MPT_PATH_* */
+  uint8_t* iters;    /* device [capacity]: minimiser iterations executed */
+  uint8_t* evals;    /* device [capacity]: residual evaluations executed */
+  float* T32;        /* device [8][capacity] or NULL: parameters before refinement */
+  int64_t capacity;
+} mpt_solutions;
+
+/* Solver schedule; NULL selects the library's defaults for the device. */
+typedef struct {
+  int32_t block;          /* threads per block (multiple of 32, <= 1024) */
+  int32_t blocks_per_sm;  /* resident blocks per SM for the persistent grid */
+  int32_t tile;           /* candidates per work-stealing tile (multiple of block) */
+  int32_t max_iters;      /* minimiser iteration cap (<= 255) */
+  int32_t refine_steps;   /* FP64 refinement steps (1 or 2) */
+  int32_t mixed_orders;   /* 1: one launch over all orders; 0: one launch per order */
+} mpt_schedule;
+
+/* Compacted valid paths (caller-owned device buffers). */
+typedef struct {
+  int64_t* cand;     /* device [capacity]: candidate index */
+  double* X;         /* device [12][capacity]: points, coordinate j of path i at X[j*capacity + i] */
+  double* T;         /* device [8][capacity]: parameters */
+  double* length;    /* device [capacity]: path length (m) */
+  double* cost;      /* device [capacity] */
+  int64_t capacity;
+} mpt_paths;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on `device` (cudaSetDevice is called).  *out owns a few KB
+ * of device scratch, grown on demand by mpt_validate. */
+int mpt_ctx_create(int device, mpt_ctx** out);
+int mpt_ctx_destroy(mpt_ctx* ctx);
+/* Number of SMs of the context's device (host value). */
+int mpt_ctx_sm_count(const mpt_ctx* ctx);
+
+/* ------------------------------------------------------------------ scene */
+
+/* Objects database D (Sec. II).  Copies the host records to the device
+ * (synchronous).  Errors: MPT_ERR_ARG for unknown kinds, non-positive
+ * scale, n_obj outside [1, MPT_MAX_OBJECTS], n_occ outside
+ * [0, MPT_MAX_OCCLUDERS]. */
+int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out);
+int mpt_scene_free(mpt_scene* scene);
+
+/* ---------------------------------------------------------- candidates */
+
+/* Candidate enumeration (Algorithm 1, all_simple_paths over the adjacency
+ * matrix of Sec. III / Fig. 5; the BS row and UE column are taken as all
+ * ones).  adj_mask: device uint8 [n_obj][n_obj] or NULL (complete graph);
+ * applied to fully enumerated orders only.  max_order in [1, 4].  The number
+ * of sequences must fit the library's table (2^24 entries); the number of
+ * candidates E * n_pairs is written to *out->count and out->order_begin; when
+ * it exceeds out->capacity, nothing beyond capacity is written.  When the
+ * count is known on the host (no mask) and exceeds capacity, the call returns
+ * MPT_ERR_CAPACITY before enqueuing anything.  With a mask the call
+ * synchronises the stream once to size its sequence table. */
+int mpt_enumerate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, int max_order,
+                  const uint8_t* adj_mask, const mpt_sampling* sampling, mpt_candidates* out,
+                  void* stream);
+
+/* Host-side count of candidates mpt_enumerate will produce without a mask
+ * (E * n_pairs); -1 on bad arguments. */
+int64_t mpt_candidate_count(const mpt_scene* scene, const mpt_endpoints* ends, int max_order,
+                            const mpt_sampling* sampling);
+
+/* ---------------------------------------------------------------- solve */
+
+/* find_minimum_path (Algorithm 1) for every candidate: Gauss-Newton with a
+ * backtracking line search on the cost of Eq. 15, with residuals of Eq. 8
+ * (divided by ||X_k - X_{k-1}||) and Eq. 9.  Reads min(*cand->count,
+ * cand->capacity) candidates on the device.  precision: MPT_FP64_PLAIN,
+ * MPT_FP32 or MPT_FP32_FP64REFINE.  out->capacity must be >= cand->capacity
+ * (MPT_ERR_CAPACITY otherwise). */
+int mpt_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
+              const mpt_candidates* cand, int precision, const mpt_schedule* schedule,
+              mpt_solutions* out, void* stream);
+
+/* ------------------------------------------------------------- validate */
+
+/* Acceptance of Algorithm 1: cost < tau (FP64), every segment longer than
+ * 1e-5 S, every point inside its object's bounds, no segment blocked by an
+ * occluder (Sec. II: bounds applied a posteriori).  Valid paths are written in
+ * candidate order to `out`; the number of valid paths goes to *d_valid_count
+ * (device int64).  If it exceeds out->capacity, only the first capacity paths
+ * are written and the full count is still reported.  Occluders are staged in
+ * shared memory with bulk asynchronous copies; a bounded wait on that copy
+ * that gives up sets the context's error flag (see mpt_ctx_check). */
+int mpt_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
+                 const mpt_candidates* cand, const mpt_solutions* sol, double tau, mpt_paths* out,
+                 int64_t* d_valid_count, void* stream);
+
+/* Reads (synchronously) and clears the context's device error flag: MPT_OK or
+ * MPT_ERR_TIMEOUT when a bounded device wait gave up since the last check. */
+int mpt_ctx_check(mpt_ctx* ctx, void* stream);
+
+/* ----------------------------------------------------------------- grad */
+
+/* Adjoint of converged paths (implicit-function theorem on rho(T, theta) = 0
+ * of Eq. 15): for each of the first min(*d_valid_count, paths->capacity)
+ * paths, with upstream weights g_len[i] (device double [capacity]) on the path
+ * length and g_pts (device double [12][capacity] or NULL) on the points,
+ * accumulates (+=, atomically) into
+ *   g_tx  device double [n_tx][3]   d/d TX position
+ *   g_rx  device double [n_rx][3]   d/d RX position
+ *   g_obj device double [n_obj]     d/d offset d of each plane <n, X> = d
+ *                                   (moved along n; other kinds get 0)
+ * Any of g_tx, g_rx, g_obj may be NULL. */
+int mpt_grad(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
+             const mpt_candidates* cand, const mpt_paths* paths, const int64_t* d_valid_count,
+             const double* g_len, const double* g_pts, double* g_tx, double* g_rx, double* g_obj,
+             void* stream);
+
+/* --------------------------------------------------------------- misc */
+
+const char* mpt_status_string(int status);
+/* FLOP model of the FP32 minimiser for a sequence of `order` objects of the
+ * given kinds, counted by running the kernel's own arithmetic on the host with
+ * a counting scalar: flops_per_eval = FP32 add/sub/mul (1) and FMA (2) of one
+ * cost + normal-equation evaluation at a trial point; flops_per_iter = those
+ * of one Cholesky factorisation and solve; sfu_per_eval = reciprocal square
+ * roots and sin/cos of one evaluation (may be NULL).  Algorithmic FLOPs of a
+ * candidate = evals * flops_per_eval + iters * flops_per_iter, with evals and
+ * iters as reported in mpt_solutions. */
+int mpt_flop_model(int order, const int32_t* kinds, double* flops_per_iter, double* flops_per_eval,
+                   double* sfu_per_eval);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPT_H_ */

@@ -1,0 +1,364 @@
+// C ABI entry points of libmpt: context, scene upload, argument checks and
+// dispatch to the kernels, status strings and the FLOP model.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "mpt_internal.cuh"
+
+// The FLOP model instantiates the __host__ __device__ kernel math with a
+// host-only counting scalar; that instantiation never runs on the device.
+#pragma nv_diag_suppress 20014
+
+namespace mpt {
+
+int64_t host_candidate_count(const mpt_scene* scene, const mpt_endpoints* ends, int max_order,
+                             const mpt_sampling* smp);
+
+int check_ends(const mpt_endpoints* e) {
+  if (!e || !e->tx || !e->rx || e->n_tx <= 0 || e->n_rx <= 0) return MPT_ERR_ARG;
+  if (e->pair_mode != 0 && e->pair_mode != 1) return MPT_ERR_ARG;
+  if (e->pair_mode == 1 && e->n_tx != e->n_rx) return MPT_ERR_ARG;
+  if (n_pairs(e) > 0xFFFFFFFFll) return MPT_ERR_ARG;
+  return MPT_OK;
+}
+
+// 24-value host record -> 16-value device record (see mpt_math.cuh).
+static bool convert_object(int kind, const double* p, double* v) {
+  for (int i = 0; i < 16; ++i) v[i] = 0.0;
+  switch (kind) {
+    case MPT_PLANE:
+      v[0] = p[4]; v[1] = p[5]; v[2] = p[6]; v[3] = p[13];
+      v[4] = p[7]; v[5] = p[8]; v[6] = p[9]; v[7] = p[14];
+      v[8] = p[10]; v[9] = p[11]; v[10] = p[12]; v[11] = p[3];
+      v[12] = p[0]; v[13] = p[1]; v[14] = p[2];
+      return p[13] >= 0 && p[14] >= 0;
+    case MPT_PARABOLOID: {
+      const double f = p[12];
+      if (!(f > 0) || !(p[13] > 0)) return false;
+      for (int j = 0; j < 3; ++j) {
+        v[4 * j + 0] = p[j];
+        v[4 * j + 1] = p[3 + j];
+        v[4 * j + 2] = p[6 + j];
+        v[4 * j + 3] = p[9 + j];
+      }
+      v[12] = 1.0 / (4.0 * f); v[13] = p[13]; v[14] = 1.0 / (2.0 * f); v[15] = f;
+      return true;
+    }
+    case MPT_LINE_EDGE:
+      v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[6];
+      v[4] = p[3]; v[5] = p[4]; v[6] = p[5]; v[7] = p[7];
+      return p[7] >= p[6];
+    case MPT_ARC_EDGE: {
+      const double a[3] = {p[3], p[4], p[5]}, u[3] = {p[7], p[8], p[9]};
+      v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[6];
+      v[4] = u[0]; v[5] = u[1]; v[6] = u[2]; v[7] = p[10];
+      v[8] = a[1] * u[2] - a[2] * u[1];
+      v[9] = a[2] * u[0] - a[0] * u[2];
+      v[10] = a[0] * u[1] - a[1] * u[0];
+      v[11] = p[11];
+      v[12] = a[0]; v[13] = a[1]; v[14] = a[2];
+      return p[6] > 0 && p[11] >= p[10];
+    }
+    default:
+      return false;
+  }
+}
+
+static bool convert_occluder(int kind, const double* p, double* v) {
+  for (int i = 0; i < 16; ++i) v[i] = 0.0;
+  if (kind == MPT_OCC_RECT) {
+    v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[9];
+    v[4] = p[3]; v[5] = p[4]; v[6] = p[5]; v[7] = p[10];
+    v[8] = p[6]; v[9] = p[7]; v[10] = p[8];
+    v[12] = p[11]; v[13] = p[12]; v[14] = p[13];
+    return true;
+  }
+  if (kind == MPT_OCC_PARABOLOID) return convert_object(MPT_PARABOLOID, p, v);
+  return false;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ------------------------------------------------------ FLOP counting --
+// Scalar that counts its FP32-pipe operations (add/sub/mul = 1, fma = 2)
+// and its special-function operations separately.
+struct Cnt {
+  float v;
+  Cnt() : v(0) {}
+  Cnt(float x) : v(x) {}   // NOLINT
+  Cnt(double x) : v((float)x) {}  // NOLINT
+  Cnt(int x) : v((float)x) {}  // NOLINT
+};
+static thread_local double g_flops = 0, g_sfu = 0;
+inline Cnt operator+(Cnt a, Cnt b) { g_flops += 1; return Cnt(a.v + b.v); }
+inline Cnt operator-(Cnt a, Cnt b) { g_flops += 1; return Cnt(a.v - b.v); }
+inline Cnt operator*(Cnt a, Cnt b) { g_flops += 1; return Cnt(a.v * b.v); }
+inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
+inline bool operator<(Cnt a, Cnt b) { return a.v < b.v; }
+inline bool operator>(Cnt a, Cnt b) { return a.v > b.v; }
+inline bool operator<=(Cnt a, Cnt b) { return a.v <= b.v; }
+inline bool operator>=(Cnt a, Cnt b) { return a.v >= b.v; }
+inline Cnt fma_(Cnt a, Cnt b, Cnt c) { g_flops += 2; return Cnt(a.v * b.v + c.v); }
+inline Cnt rsq(Cnt a) { g_sfu += 1; return Cnt(1.0f / std::sqrt(a.v)); }
+inline void sincos_(Cnt x, Cnt& s, Cnt& c) { g_sfu += 2; s = Cnt(std::sin(x.v)); c = Cnt(std::cos(x.v)); }
+
+template <int N>
+static void count_model(const int32_t* kinds, double* f_eval, double* f_iter, double* sfu_eval) {
+  int kind[N];
+  Rec<Cnt> rec[N];
+  Cnt prm[2 * N];
+  for (int k = 0; k < N; ++k) {
+    kind[k] = kinds[k];
+    for (int i = 0; i < 16; ++i) rec[k].v[i] = Cnt(0.1f * (i + 1) + k);
+    rec[k].v[3] = Cnt(2.0f);
+    prm[2 * k] = Cnt(0.3f + k);
+    prm[2 * k + 1] = Cnt(0.7f - k);
+  }
+  v3<Cnt> A = mk(Cnt(-5.0f), Cnt(1.0f), Cnt(3.0f)), B = mk(Cnt(6.0f), Cnt(-2.0f), Cnt(4.0f));
+  constexpr int Q = 2 * N;
+  Cnt jtj[Q * (Q + 1) / 2], g[Q], x[Q];
+  bool ok;
+  g_flops = 0;
+  g_sfu = 0;
+  eval_path<N, Cnt, Cnt, true>(kind, rec, prm, A, B, jtj, g, ok);
+  // trial point update alpha * dlt + prm
+  *f_eval = g_flops + 2.0 * Q;
+  *sfu_eval = g_sfu;
+  for (int i = 0; i < Q * (Q + 1) / 2; ++i) jtj[i] = Cnt(i == 0 ? 4.0f : 0.5f);
+  g_flops = 0;
+  cholesky<Q, Cnt>(jtj, Cnt(1e-6f));
+  chol_solve<Q, Cnt>(jtj, g, x);
+  *f_iter = g_flops;
+}
+
+}  // namespace mpt
+
+using namespace mpt;
+
+extern "C" {
+
+const char* mpt_status_string(int status) {
+  switch (status) {
+    case MPT_OK: return "MPT_OK";
+    case MPT_ERR_ARG: return "MPT_ERR_ARG: invalid argument";
+    case MPT_ERR_CUDA: return "MPT_ERR_CUDA: CUDA runtime error";
+    case MPT_ERR_CAPACITY: return "MPT_ERR_CAPACITY: output buffer too small";
+    case MPT_ERR_TIMEOUT: return "MPT_ERR_TIMEOUT: a bounded device wait gave up";
+    case MPT_ERR_UNSUPPORTED: return "MPT_ERR_UNSUPPORTED: request not supported";
+    default: return "unknown status";
+  }
+}
+
+int mpt_ctx_create(int device, mpt_ctx** out) {
+  if (!out) return MPT_ERR_ARG;
+  *out = nullptr;
+  int n_dev = 0;
+  MPT_CUDA_TRY(cudaGetDeviceCount(&n_dev));
+  if (device < 0 || device >= n_dev) return MPT_ERR_ARG;
+  MPT_CUDA_TRY(cudaSetDevice(device));
+  mpt_ctx* c = new mpt_ctx();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, 64 * sizeof(unsigned long long) + 256);
+  if (e != cudaSuccess) {
+    delete c;
+    return MPT_ERR_CUDA;
+  }
+  cudaMemset(p, 0, 64 * sizeof(unsigned long long) + 256);
+  c->counters = reinterpret_cast<unsigned long long*>(p);
+  c->err_flag = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(p) + 64 * sizeof(unsigned long long));
+  c->vscratch = nullptr;
+  c->vscratch_bytes = 0;
+  *out = c;
+  return MPT_OK;
+}
+
+int mpt_ctx_destroy(mpt_ctx* ctx) {
+  if (!ctx) return MPT_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->vscratch) cudaFree(ctx->vscratch);
+  cudaFree(ctx->counters);
+  delete ctx;
+  return MPT_OK;
+}
+
+int mpt_ctx_sm_count(const mpt_ctx* ctx) { return ctx ? ctx->sms : 0; }
+
+int mpt_ctx_check(mpt_ctx* ctx, void* stream) {
+  if (!ctx) return MPT_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int flag = 0;
+  MPT_CUDA_TRY(cudaMemcpyAsync(&flag, ctx->err_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MPT_CUDA_TRY(cudaStreamSynchronize(st));
+  if (flag != 0) MPT_CUDA_TRY(cudaMemsetAsync(ctx->err_flag, 0, sizeof(int), st));
+  return flag == 0 ? MPT_OK : flag;
+}
+
+int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) {
+  if (!ctx || !desc || !out) return MPT_ERR_ARG;
+  *out = nullptr;
+  const int no = desc->n_obj, nc = desc->n_occ;
+  if (no < 1 || no > MPT_MAX_OBJECTS || nc < 0 || nc > MPT_MAX_OCCLUDERS) return MPT_ERR_ARG;
+  if (!desc->obj_kind || !desc->obj_param || (nc > 0 && (!desc->occ_kind || !desc->occ_param)))
+    return MPT_ERR_ARG;
+  if (!(desc->scale > 0) || !std::isfinite(desc->scale)) return MPT_ERR_ARG;
+  std::vector<double> ov((size_t)no * 16), cv((size_t)nc * 16);
+  for (int o = 0; o < no; ++o)
+    if (!convert_object(desc->obj_kind[o], desc->obj_param + (size_t)MPT_RECORD * o, &ov[(size_t)16 * o]))
+      return MPT_ERR_ARG;
+  for (int o = 0; o < nc; ++o)
+    if (!convert_occluder(desc->occ_kind[o], desc->occ_param + (size_t)MPT_RECORD * o, &cv[(size_t)16 * o]))
+      return MPT_ERR_ARG;
+  // field-major device layout: float4 f of object o at [f * n + o]
+  std::vector<float> o32((size_t)no * 16), c32((size_t)nc * 16);
+  std::vector<double> o64((size_t)no * 16), c64((size_t)nc * 16);
+  for (int o = 0; o < no; ++o)
+    for (int i = 0; i < 16; ++i) {
+      o32[((size_t)(i / 4) * no + o) * 4 + (i % 4)] = (float)ov[(size_t)16 * o + i];
+      o64[((size_t)(i / 2) * no + o) * 2 + (i % 2)] = ov[(size_t)16 * o + i];
+    }
+  for (int o = 0; o < nc; ++o)
+    for (int i = 0; i < 16; ++i) {
+      c32[((size_t)(i / 4) * nc + o) * 4 + (i % 4)] = (float)cv[(size_t)16 * o + i];
+      c64[((size_t)(i / 2) * nc + o) * 2 + (i % 2)] = cv[(size_t)16 * o + i];
+    }
+  // plane objects whose rectangle is also an occluder
+  std::vector<int32_t> obj_occ(no, -1);
+  for (int o = 0; o < no; ++o) {
+    if (desc->obj_kind[o] != MPT_PLANE) continue;
+    const double* a = &ov[(size_t)16 * o];
+    for (int q = 0; q < nc; ++q) {
+      if (desc->occ_kind[q] != MPT_OCC_RECT) continue;
+      const double* b = &cv[(size_t)16 * q];
+      // same corner, axes and extents (values 0..10 of both records)
+      bool same = true;
+      for (int i = 0; i < 11; ++i) same = same && a[i] == b[i];
+      if (same) { obj_occ[o] = q; break; }
+    }
+  }
+  const size_t s_kind = align256((size_t)no * 4), s_o32 = align256((size_t)no * 64),
+               s_o64 = align256((size_t)no * 128), s_ck = align256((size_t)nc * 4 + 4),
+               s_c32 = align256((size_t)nc * 64 + 16), s_c64 = align256((size_t)nc * 128 + 16),
+               s_oo = align256((size_t)no * 4);
+  const size_t total = s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo;
+  MPT_CUDA_TRY(cudaSetDevice(ctx->device));
+  void* mem = nullptr;
+  MPT_CUDA_TRY(cudaMalloc(&mem, total));
+  unsigned char* b = reinterpret_cast<unsigned char*>(mem);
+  mpt_scene* s = new mpt_scene();
+  s->ctx = ctx;
+  s->alloc = mem;
+  s->n_obj = no;
+  s->host_kind = reinterpret_cast<int32_t*>(std::malloc(sizeof(int32_t) * no));
+  std::memcpy(s->host_kind, desc->obj_kind, sizeof(int32_t) * no);
+  size_t off = 0;
+  auto put = [&](const void* src, size_t n, size_t span) -> void* {
+    void* dst = b + off;
+    if (n) cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
+    off += span;
+    return dst;
+  };
+  DevScene& d = s->d;
+  d.n_obj = no;
+  d.n_occ = nc;
+  d.kind = reinterpret_cast<const int32_t*>(put(desc->obj_kind, (size_t)no * 4, s_kind));
+  d.o32 = reinterpret_cast<const float4*>(put(o32.data(), (size_t)no * 64, s_o32));
+  d.o64 = reinterpret_cast<const double2*>(put(o64.data(), (size_t)no * 128, s_o64));
+  d.occ_kind = reinterpret_cast<const int32_t*>(put(nc ? desc->occ_kind : nullptr, (size_t)nc * 4, s_ck));
+  d.c32 = reinterpret_cast<const float4*>(put(c32.data(), (size_t)nc * 64, s_c32));
+  d.c64 = reinterpret_cast<const double2*>(put(c64.data(), (size_t)nc * 128, s_c64));
+  d.obj_occ = reinterpret_cast<const int32_t*>(put(obj_occ.data(), (size_t)no * 4, s_oo));
+  d.scale = desc->scale;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFree(mem);
+    std::free(s->host_kind);
+    delete s;
+    return MPT_ERR_CUDA;
+  }
+  *out = s;
+  return MPT_OK;
+}
+
+int mpt_scene_free(mpt_scene* scene) {
+  if (!scene) return MPT_ERR_ARG;
+  cudaSetDevice(scene->ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(scene->alloc);
+  std::free(scene->host_kind);
+  delete scene;
+  return MPT_OK;
+}
+
+int64_t mpt_candidate_count(const mpt_scene* scene, const mpt_endpoints* ends, int max_order,
+                            const mpt_sampling* sampling) {
+  return host_candidate_count(scene, ends, max_order, sampling);
+}
+
+int mpt_enumerate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, int max_order,
+                  const uint8_t* adj_mask, const mpt_sampling* sampling, mpt_candidates* out, void* stream) {
+  if (!ctx || !scene || !out || !out->rec || !out->count || !out->order_begin || out->capacity < 0)
+    return MPT_ERR_ARG;
+  if (check_ends(ends) != MPT_OK) return MPT_ERR_ARG;
+  return launch_enumerate(ctx, scene, ends, max_order, adj_mask, sampling, out,
+                          reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mpt_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
+              int precision, const mpt_schedule* schedule, mpt_solutions* out, void* stream) {
+  if (!ctx || !scene || !cand || !out || !cand->rec || !cand->order_begin || !out->T || !out->cost ||
+      !out->status || !out->iters || !out->evals)
+    return MPT_ERR_ARG;
+  if (check_ends(ends) != MPT_OK) return MPT_ERR_ARG;
+  if (precision != MPT_FP64_PLAIN && precision != MPT_FP32 && precision != MPT_FP32_FP64REFINE) return MPT_ERR_ARG;
+  if (schedule && (schedule->max_iters < 0 || schedule->refine_steps < 0 || schedule->blocks_per_sm < 0))
+    return MPT_ERR_ARG;
+  if (out->capacity < cand->capacity) return MPT_ERR_CAPACITY;
+  if (cand->capacity == 0) return MPT_OK;
+  return launch_solve(ctx, scene, ends, cand, precision, schedule, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mpt_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
+                 const mpt_solutions* sol, double tau, mpt_paths* out, int64_t* d_valid_count, void* stream) {
+  if (!ctx || !scene || !cand || !sol || !out || !d_valid_count || !cand->rec || !cand->count || !sol->T ||
+      !sol->cost || !sol->status || !out->cand || !out->X || !out->T || !out->length || !out->cost)
+    return MPT_ERR_ARG;
+  if (check_ends(ends) != MPT_OK) return MPT_ERR_ARG;
+  if (!(tau > 0) || out->capacity < 0 || sol->capacity < cand->capacity) return MPT_ERR_ARG;
+  return launch_validate(ctx, scene, ends, cand, sol, tau, out, d_valid_count,
+                         reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mpt_grad(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
+             const mpt_paths* paths, const int64_t* d_valid_count, const double* g_len, const double* g_pts,
+             double* g_tx, double* g_rx, double* g_obj, void* stream) {
+  if (!ctx || !scene || !cand || !paths || !d_valid_count || !g_len || !cand->rec || !paths->cand || !paths->T)
+    return MPT_ERR_ARG;
+  if (check_ends(ends) != MPT_OK) return MPT_ERR_ARG;
+  return launch_grad(ctx, scene, ends, cand, paths, d_valid_count, g_len, g_pts, g_tx, g_rx, g_obj,
+                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mpt_flop_model(int order, const int32_t* kinds, double* flops_per_iter, double* flops_per_eval,
+                   double* sfu_per_eval) {
+  if (order < 1 || order > 4 || !kinds || !flops_per_iter || !flops_per_eval) return MPT_ERR_ARG;
+  for (int k = 0; k < order; ++k)
+    if (kinds[k] < 0 || kinds[k] > 3) return MPT_ERR_ARG;
+  double fe = 0, fi = 0, sfu = 0;
+  switch (order) {
+    case 1: count_model<1>(kinds, &fe, &fi, &sfu); break;
+    case 2: count_model<2>(kinds, &fe, &fi, &sfu); break;
+    case 3: count_model<3>(kinds, &fe, &fi, &sfu); break;
+    default: count_model<4>(kinds, &fe, &fi, &sfu); break;
+  }
+  *flops_per_iter = fi;
+  *flops_per_eval = fe;
+  if (sfu_per_eval) *sfu_per_eval = sfu;
+  return MPT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Internal declarations shared by the CUDA translation units of libmpt.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "../../include/mpt.h"
+#include "mpt_math.cuh"
+
+namespace mpt {
+
+// Device view of a scene.  Objects are stored field-major: field f (a float4
+// or double2 of the 16-value record) of object o at o32[f * n_obj + o].  The
+// solver reads the objects of its candidate's sequence, which every lane of
+// a warp shares, so each field load is one broadcast transaction.
+struct DevScene {
+  int n_obj, n_occ;
+  const int32_t* kind;      // [n_obj]
+  const float4* o32;        // [4][n_obj]
+  const double2* o64;       // [8][n_obj]
+  const int32_t* occ_kind;  // [n_occ]
+  const float4* c32;        // [4][n_occ]
+  const double2* c64;       // [8][n_occ]
+  const int32_t* obj_occ;   // [n_obj]: occluder holding this plane's rectangle, or -1
+  double scale;
+};
+
+struct DevEnds {
+  const double* tx;
+  const double* rx;
+  int n_tx, n_rx, pair_mode;
+};
+
+__device__ __forceinline__ void pair_ends(const DevEnds& e, uint32_t p, int& it, int& ir) {
+  if (e.pair_mode == 0) {
+    it = (int)(p / (uint32_t)e.n_rx);
+    ir = (int)(p % (uint32_t)e.n_rx);
+  } else {
+    it = ir = (int)p;
+  }
+}
+
+__device__ __forceinline__ Rec<float> load_obj32(const DevScene& s, int o) {
+  Rec<float> r;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    float4 q = __ldg(&s.o32[f * s.n_obj + o]);
+    r.v[4 * f] = q.x; r.v[4 * f + 1] = q.y; r.v[4 * f + 2] = q.z; r.v[4 * f + 3] = q.w;
+  }
+  return r;
+}
+__device__ __forceinline__ Rec<double> load_obj64(const DevScene& s, int o) {
+  Rec<double> r;
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    double2 q = __ldg(&s.o64[f * s.n_obj + o]);
+    r.v[2 * f] = q.x; r.v[2 * f + 1] = q.y;
+  }
+  return r;
+}
+
+// SplitMix64 output function (Steele, Lea, Flood 2014): mixes x + gamma.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Decoded candidate record (see mpt_candidates in mpt.h).
+struct Cand {
+  uint32_t pair;
+  int ids[4];
+  int order, start;
+};
+__device__ __forceinline__ Cand decode(uint4 r) {
+  Cand c;
+  c.pair = r.x;
+  c.ids[0] = (int)(r.y & 0xFFFFu);
+  c.ids[1] = (int)(r.y >> 16);
+  c.ids[2] = (int)(r.z & 0xFFFFu);
+  c.ids[3] = (int)(r.z >> 16);
+  c.order = (int)(r.w & 0xFFu);
+  c.start = (int)((r.w >> 8) & 0xFFu);
+  return c;
+}
+
+// Candidate indices the scene and endpoints can serve (guards against
+// records that do not belong to this scene).
+__device__ __forceinline__ bool cand_in_range(const DevScene& sc, const DevEnds& ep, const Cand& cd) {
+  if (cd.order < 1 || cd.order > 4) return false;
+  for (int k = 0; k < cd.order; ++k)
+    if (cd.ids[k] >= sc.n_obj) return false;
+  int it, ir;
+  pair_ends(ep, cd.pair, it, ir);
+  return it < ep.n_tx && ir < ep.n_rx;
+}
+
+constexpr int SOLVE_BLOCK = 128;
+
+}  // namespace mpt
+
+// ------------------------------------------------------------- handles --
+struct mpt_ctx {
+  int device;
+  int sms;
+  // small persistent scratch: work-stealing counters and an error flag
+  unsigned long long* counters;  // [64]
+  int* err_flag;                 // [1]
+  // validate scratch, grown on demand
+  void* vscratch;
+  size_t vscratch_bytes;
+};
+
+struct mpt_scene {
+  mpt_ctx* ctx;
+  mpt::DevScene d;
+  void* alloc;             // one device allocation holding every array
+  int32_t* host_kind;      // host copy of the kinds
+  int n_obj;
+};
+
+#define MPT_CUDA_TRY(expr)                                                 \
+  do {                                                                     \
+    cudaError_t e_ = (expr);                                               \
+    if (e_ != cudaSuccess) {                                               \
+      std::fprintf(stderr, "libmpt: %s failed: %s\n", #expr, cudaGetErrorString(e_)); \
+      return MPT_ERR_CUDA;                                                 \
+    }                                                                      \
+  } while (0)
+
+#define MPT_LAUNCH_CHECK()                                                  \
+  do {                                                                      \
+    cudaError_t e_ = cudaGetLastError();                                    \
+    if (e_ != cudaSuccess) {                                                \
+      std::fprintf(stderr, "libmpt: launch failed: %s\n", cudaGetErrorString(e_)); \
+      return MPT_ERR_CUDA;                                                  \
+    }                                                                       \
+  } while (0)
+
+namespace mpt {
+inline DevEnds dev_ends(const mpt_endpoints* e) {
+  DevEnds d;
+  d.tx = e->tx;
+  d.rx = e->rx;
+  d.n_tx = e->n_tx;
+  d.n_rx = e->n_rx;
+  d.pair_mode = e->pair_mode;
+  return d;
+}
+inline int64_t n_pairs(const mpt_endpoints* e) {
+  return e->pair_mode == 0 ? (int64_t)e->n_tx * e->n_rx : (int64_t)e->n_tx;
+}
+int check_ends(const mpt_endpoints* e);
+// launchers implemented in the .cu files
+int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
+                 const mpt_candidates* cand, int precision, const mpt_schedule* sch,
+                 mpt_solutions* out, cudaStream_t st);
+int launch_enumerate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, int max_order,
+                     const uint8_t* adj, const mpt_sampling* smp, mpt_candidates* out, cudaStream_t st);
+int launch_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
+                    const mpt_candidates* cand, const mpt_solutions* sol, double tau, mpt_paths* out,
+                    int64_t* d_valid_count, cudaStream_t st);
+int launch_grad(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
+                const mpt_candidates* cand, const mpt_paths* paths, const int64_t* d_valid_count,
+                const double* g_len, const double* g_pts, double* g_tx, double* g_rx, double* g_obj,
+                cudaStream_t st);
+}  // namespace mpt

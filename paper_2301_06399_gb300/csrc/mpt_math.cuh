@@ -1,0 +1,372 @@
+// Device math of the MPT solver: parametric points (Eqs. 13-14), the law
+// residuals (Eq. 8 divided by ||X_k - X_{k-1}||, Eq. 9), their hand-derived
+// Jacobian with respect to the object parameters, and the accumulation of
+// the Gauss-Newton normal equations J^T J, J^T rho of Eq. 15.
+//
+// Everything is templated on two scalar types: R for the geometry and the
+// residual, J for the Jacobian.  (float, float) is the FP32 iteration,
+// (double, float) the mixed FP64 refinement, (double, double) the plain FP64
+// method.  The host instantiates the same code with a counting type to give
+// the FLOP model of the kernels.
+#pragma once
+
+#include <cstdint>
+
+#if defined(__CUDACC__)
+#define MPT_HD __host__ __device__ __forceinline__
+#else
+#define MPT_HD inline
+#endif
+
+namespace mpt {
+
+// ------------------------------------------------------------- scalars --
+MPT_HD float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+MPT_HD double fma_(double a, double b, double c) { return fma(a, b, c); }
+
+// 1/sqrt(x).  FP32: the hardware reciprocal square root.  FP64: an FP32 seed
+// refined by two Newton-Raphson steps y <- y (3 - x y^2) / 2 (each step
+// squares the relative error: ~1e-7 -> ~1e-14 -> below double rounding),
+// which keeps the FP64 path off the slow double-precision divide and sqrt.
+MPT_HD float rsq(float x) {
+#if defined(__CUDA_ARCH__)
+  return rsqrtf(x);
+#else
+  return 1.0f / sqrtf(x);
+#endif
+}
+MPT_HD double rsq(double x) {
+  double y = (double)rsq((float)x);
+  double h = 0.5 * x;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+
+MPT_HD void sincos_(float x, float& s, float& c) {
+#if defined(__CUDA_ARCH__)
+  sincosf(x, &s, &c);
+#else
+  s = sinf(x);
+  c = cosf(x);
+#endif
+}
+MPT_HD void sincos_(double x, double& s, double& c) {
+#if defined(__CUDA_ARCH__)
+  sincos(x, &s, &c);
+#else
+  s = ::sin(x);
+  c = ::cos(x);
+#endif
+}
+
+// --------------------------------------------------------------- vectors --
+template <class T>
+struct v3 {
+  T x, y, z;
+};
+template <class T> MPT_HD v3<T> mk(T x, T y, T z) { v3<T> r; r.x = x; r.y = y; r.z = z; return r; }
+template <class T> MPT_HD v3<T> operator+(const v3<T>& a, const v3<T>& b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+template <class T> MPT_HD v3<T> operator-(const v3<T>& a, const v3<T>& b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+template <class T> MPT_HD v3<T> operator-(const v3<T>& a) { return mk(-a.x, -a.y, -a.z); }
+template <class T> MPT_HD v3<T> operator*(const v3<T>& a, T s) { return mk(a.x * s, a.y * s, a.z * s); }
+template <class T> MPT_HD T dot(const v3<T>& a, const v3<T>& b) { return fma_(a.x, b.x, fma_(a.y, b.y, a.z * b.z)); }
+// a + s * b
+template <class T> MPT_HD v3<T> axpy(T s, const v3<T>& b, const v3<T>& a) {
+  return mk(fma_(s, b.x, a.x), fma_(s, b.y, a.y), fma_(s, b.z, a.z));
+}
+template <class T> MPT_HD v3<T> cross(const v3<T>& a, const v3<T>& b) {
+  return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+template <class D, class S> MPT_HD v3<D> cvt(const v3<S>& a) { return mk(D(a.x), D(a.y), D(a.z)); }
+
+// ------------------------------------------------------------ scene record --
+// 16 values per object (same layout in FP32 and FP64 copies):
+//   plane       O.xyz U | u.xyz V | v.xyz d | n.xyz 0
+//   paraboloid  c0.xyz t.x | c1.xyz t.y | c2.xyz t.z | 1/(4f) rho 1/(2f) f
+//                 (c_j = column j of R: local axes in world)
+//   line edge   P.xyz t0 | e.xyz t1 | 0 | 0
+//   arc edge    C.xyz Rc | u.xyz phi0 | v.xyz phi1 | a.xyz 0   (v = a x u)
+// Occluders: rectangle O.xyz U | u.xyz V | v.xyz 0 | n.xyz 0, paraboloid as above.
+enum { K_PLANE = 0, K_PARAB = 1, K_LINE = 2, K_ARC = 3 };
+
+template <class T>
+struct Rec {
+  T v[16];
+  MPT_HD v3<T> f3(int i) const { return mk(v[i], v[i + 1], v[i + 2]); }
+};
+
+MPT_HD bool is_edge(int kind) { return kind == K_LINE || kind == K_ARC; }
+
+// ------------------------------------------------------ parametric points --
+// Point of an object at parameters (s, t) and its tangents dX/ds, dX/dt
+// (Eqs. 13, 14).  Edges use s only; their second tangent is zero.
+template <class T>
+struct PointT {
+  v3<T> X, w0, w1;
+};
+
+template <class T, bool TANGENTS>
+MPT_HD PointT<T> point_at(int kind, const Rec<T>& r, T s, T t) {
+  PointT<T> p;
+  const T zero = T(0);
+  p.w1 = mk(zero, zero, zero);
+  if (kind == K_PLANE) {
+    p.X = axpy(t, r.f3(8), axpy(s, r.f3(4), r.f3(0)));
+    if (TANGENTS) { p.w0 = r.f3(4); p.w1 = r.f3(8); }
+  } else if (kind == K_PARAB) {
+    const T q4 = r.v[12], q2 = r.v[14];
+    T h = (s * s + t * t) * q4;
+    v3<T> base = mk(r.v[3], r.v[7], r.v[11]);
+    p.X = axpy(h, r.f3(8), axpy(t, r.f3(4), axpy(s, r.f3(0), base)));
+    if (TANGENTS) {
+      p.w0 = axpy(s * q2, r.f3(8), r.f3(0));
+      p.w1 = axpy(t * q2, r.f3(8), r.f3(4));
+    }
+  } else if (kind == K_LINE) {
+    p.X = axpy(s, r.f3(4), r.f3(0));
+    if (TANGENTS) p.w0 = r.f3(4);
+  } else {
+    T sn, cs;
+    sincos_(s, sn, cs);
+    const T Rc = r.v[3];
+    p.X = axpy(Rc * sn, r.f3(8), axpy(Rc * cs, r.f3(4), r.f3(0)));
+    if (TANGENTS) p.w0 = axpy(Rc * cs, r.f3(8), r.f3(4) * (-Rc * sn));
+  }
+  return p;
+}
+
+// ---------------------------------------------------- residual + normal eqs --
+// Packed lower-triangular index of (i, j), i >= j.
+MPT_HD constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+template <int N>
+struct NormalEq {
+  static constexpr int Q = 2 * N;
+  static constexpr int P = Q * (Q + 1) / 2;
+};
+
+// Adds one column block's contribution: for the (up to) six parameter
+// columns of interaction k (previous point, this point, next point), the
+// column vectors col[c] (3 rows for reflection, 1 for diffraction) give
+// J^T J entries <col[a], col[b]> and J^T rho entries <col[a], rho>.
+template <int N, int ROWS, class J>
+MPT_HD void accumulate(int k, const J (&col)[6][ROWS], const bool (&live)[6], const J (&rho)[ROWS],
+                       J* jtj, J* g) {
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const int ga = 2 * (k - 1) + a;  // parameter index of column a
+    if (ga < 0 || ga >= 2 * N || !live[a]) continue;
+    J ga_acc = J(0);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) ga_acc = fma_(col[a][r], rho[r], ga_acc);
+    g[ga] = g[ga] + ga_acc;
+#pragma unroll
+    for (int b = 0; b <= a; ++b) {
+      const int gb = 2 * (k - 1) + b;
+      if (gb < 0 || gb >= 2 * N || !live[b]) continue;
+      J acc = J(0);
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) acc = fma_(col[a][r], col[b][r], acc);
+      jtj[tri(ga, gb)] = jtj[tri(ga, gb)] + acc;
+    }
+  }
+}
+
+// Evaluates the cost of Eq. 15 at parameters prm (slot 2k, 2k+1 for
+// interaction k; edges use slot 2k) and, when WANT_J, accumulates the normal
+// equations J^T J (packed, Q = 2N) and g = J^T rho.  A = TX, B = RX.
+// Returns the cost; `ok` is false when a segment has zero length.
+template <int N, class R, class J, bool WANT_J>
+MPT_HD R eval_path(const int (&kind)[N], const Rec<R> (&rec)[N], const R (&prm)[2 * N], const v3<R>& A,
+                   const v3<R>& B, J* jtj, J* g, bool& ok) {
+  PointT<R> pt[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) pt[k] = point_at<R, WANT_J>(kind[k], rec[k], prm[2 * k], prm[2 * k + 1]);
+  // segment unit vectors u[j] = (X_{j+1} - X_j)/||.||, inverse lengths il[j]
+  v3<R> u[N + 1];
+  R il[N + 1];
+  ok = true;
+#pragma unroll
+  for (int j = 0; j <= N; ++j) {
+    const v3<R> a = (j == 0) ? A : pt[j - 1].X;
+    const v3<R> b = (j == N) ? B : pt[j].X;
+    v3<R> d = b - a;
+    R l2 = dot(d, d);
+    ok = ok && (l2 > R(0));
+    il[j] = rsq(l2);
+    u[j] = d * il[j];
+  }
+  if (WANT_J) {
+#pragma unroll
+    for (int i = 0; i < NormalEq<N>::P; ++i) jtj[i] = J(0);
+#pragma unroll
+    for (int i = 0; i < 2 * N; ++i) g[i] = J(0);
+  }
+  R cost = R(0);
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const v3<R>& ih = u[k];      // incident direction (into X_k)
+    const v3<R>& rh = u[k + 1];  // departing direction
+    if (!is_edge(kind[k])) {
+      // ---- reflection: rho = r_hat - i_hat + 2 <i_hat, n> n  (Eq. 8 / ||i||)
+      v3<R> nh;
+      R inv_nn = R(0);
+      v3<R> nraw;
+      if (kind[k] == K_PLANE) {
+        nh = rec[k].f3(12);
+      } else {
+        // n = c2 - (s/(2f)) c0 - (t/(2f)) c1  (gradient of the implicit
+        // paraboloid, Eq. 2, up to sign and scale)
+        const R q2 = rec[k].v[14];
+        nraw = axpy(-prm[2 * k + 1] * q2, rec[k].f3(4), axpy(-prm[2 * k] * q2, rec[k].f3(0), rec[k].f3(8)));
+        inv_nn = rsq(dot(nraw, nraw));
+        nh = nraw * inv_nn;
+      }
+      const R c = dot(ih, nh);
+      v3<R> rho = axpy(R(2) * c, nh, rh - ih);
+      cost = fma_(rho.x, rho.x, fma_(rho.y, rho.y, fma_(rho.z, rho.z, cost)));
+      if (WANT_J) {
+        const v3<J> iJ = cvt<J>(ih), rJ = cvt<J>(rh), nJ = cvt<J>(nh);
+        const J ia = J(il[k]), ib = J(il[k + 1]);
+        J col[6][3];
+        bool live[6];
+        // P_i w / ||i|| and P_r w / ||r||
+        auto Pi = [&](const v3<J>& w) { return axpy(-dot(iJ, w), iJ, w) * ia; };
+        auto Pr = [&](const v3<J>& w) { return axpy(-dot(rJ, w), rJ, w) * ib; };
+        auto H = [&](const v3<J>& w) { return axpy(J(-2) * dot(nJ, w), nJ, w); };
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          // previous point (k-1): H P_i w / ||i||
+          live[j] = (k >= 1) && (j == 0 || !is_edge(kind[k > 0 ? k - 1 : 0]));
+          if (k >= 1) {
+            const v3<J> w = cvt<J>(j == 0 ? pt[k - 1].w0 : pt[k - 1].w1);
+            v3<J> v = H(Pi(w));
+            col[j][0] = v.x; col[j][1] = v.y; col[j][2] = v.z;
+          } else {
+            col[j][0] = col[j][1] = col[j][2] = J(0);
+          }
+          // this point: -P_r w/||r|| - H P_i w/||i|| (+ normal variation)
+          live[2 + j] = true;
+          {
+            const v3<J> w = cvt<J>(j == 0 ? pt[k].w0 : pt[k].w1);
+            v3<J> v = -(Pr(w) + H(Pi(w)));
+            if (kind[k] == K_PARAB) {
+              // d/dT of 2 <i,n> n through n: 2 (<i, dn> n + <i, n> dn),
+              // dn = (I - n n^T) dn_raw / ||n_raw||, dn_raw = -c_j / (2f)
+              const J q2 = J(rec[k].v[14]);
+              const v3<J> craw = cvt<J>(j == 0 ? rec[k].f3(0) : rec[k].f3(4)) * (-q2);
+              const v3<J> dn = axpy(-dot(nJ, craw), nJ, craw) * J(inv_nn);
+              v = axpy(J(2) * dot(iJ, dn), nJ, v);
+              v = axpy(J(2) * J(c), dn, v);
+            }
+            col[2 + j][0] = v.x; col[2 + j][1] = v.y; col[2 + j][2] = v.z;
+          }
+          // next point (k+1): P_r w / ||r||
+          live[4 + j] = (k + 1 < N) && (j == 0 || !is_edge(kind[k + 1 < N ? k + 1 : k]));
+          if (k + 1 < N) {
+            const v3<J> w = cvt<J>(j == 0 ? pt[k + 1].w0 : pt[k + 1].w1);
+            v3<J> v = Pr(w);
+            col[4 + j][0] = v.x; col[4 + j][1] = v.y; col[4 + j][2] = v.z;
+          } else {
+            col[4 + j][0] = col[4 + j][1] = col[4 + j][2] = J(0);
+          }
+        }
+        const J rr[3] = {J(rho.x), J(rho.y), J(rho.z)};
+        accumulate<N, 3, J>(k, col, live, rr, jtj, g);
+      }
+    } else {
+      // ---- diffraction: rho = <i_hat, e> - <r_hat, e>  (Eq. 9)
+      v3<R> eh;
+      v3<R> de;  // d e / d phi for arcs
+      if (kind[k] == K_LINE) {
+        eh = rec[k].f3(4);
+      } else {
+        R sn, cs;
+        sincos_(prm[2 * k], sn, cs);
+        eh = axpy(cs, rec[k].f3(8), rec[k].f3(4) * (-sn));
+        de = axpy(-sn, rec[k].f3(8), rec[k].f3(4) * (-cs));
+      }
+      const R rho = dot(ih, eh) - dot(rh, eh);
+      cost = fma_(rho, rho, cost);
+      if (WANT_J) {
+        const v3<J> iJ = cvt<J>(ih), rJ = cvt<J>(rh), eJ = cvt<J>(eh);
+        const J ia = J(il[k]), ib = J(il[k + 1]);
+        const J ei = dot(eJ, iJ), er = dot(eJ, rJ);
+        // <e, P_i w>/||i|| = (<e,w> - <e,i><i,w>)/||i||, same for r
+        auto ePi = [&](const v3<J>& w) { return (dot(eJ, w) - ei * dot(iJ, w)) * ia; };
+        auto ePr = [&](const v3<J>& w) { return (dot(eJ, w) - er * dot(rJ, w)) * ib; };
+        J col[6][1];
+        bool live[6];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          live[j] = (k >= 1) && (j == 0 || !is_edge(kind[k > 0 ? k - 1 : 0]));
+          col[j][0] = (k >= 1) ? -ePi(cvt<J>(j == 0 ? pt[k > 0 ? k - 1 : 0].w0 : pt[k > 0 ? k - 1 : 0].w1)) : J(0);
+          live[4 + j] = (k + 1 < N) && (j == 0 || !is_edge(kind[k + 1 < N ? k + 1 : k]));
+          col[4 + j][0] = (k + 1 < N) ? -ePr(cvt<J>(j == 0 ? pt[k + 1 < N ? k + 1 : k].w0
+                                                            : pt[k + 1 < N ? k + 1 : k].w1))
+                                      : J(0);
+        }
+        {
+          const v3<J> w = cvt<J>(pt[k].w0);
+          J v = ePi(w) + ePr(w);
+          if (kind[k] == K_ARC) v = v + dot(iJ - rJ, cvt<J>(de));  // edge direction variation
+          col[2][0] = v;
+          live[2] = true;
+          col[3][0] = J(0);
+          live[3] = false;
+        }
+        const J rr[1] = {J(rho)};
+        accumulate<N, 1, J>(k, col, live, rr, jtj, g);
+      }
+    }
+  }
+  return cost;
+}
+
+// Cholesky factorisation of the packed Q x Q matrix in place (lower), with
+// relative diagonal damping mu.  Returns false when a pivot is not positive.
+template <int Q, class J>
+MPT_HD bool cholesky(J* a, J mu) {
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    J d = a[tri(j, j)];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d = fma_(-a[tri(j, k)], a[tri(j, k)], d);
+    d = d + mu * a[tri(j, j)] + J(1e-30f);
+    ok = ok && (d > J(0));
+    const J inv = rsq(d > J(0) ? d : J(1));
+    a[tri(j, j)] = inv;  // store 1/L_jj
+#pragma unroll
+    for (int i = j + 1; i < Q; ++i) {
+      J s = a[tri(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s = fma_(-a[tri(i, k)], a[tri(j, k)], s);
+      a[tri(i, j)] = s * inv;
+    }
+  }
+  return ok;
+}
+
+// Solves (L L^T) x = -g with the factor from cholesky() (diagonal holds 1/L_jj).
+template <int Q, class J>
+MPT_HD void chol_solve(const J* a, const J* g, J* x) {
+  J y[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    J s = -g[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s = fma_(-a[tri(i, k)], y[k], s);
+    y[i] = s * a[tri(i, i)];
+  }
+#pragma unroll
+  for (int i = Q - 1; i >= 0; --i) {
+    J s = y[i];
+#pragma unroll
+    for (int k = i + 1; k < Q; ++k) s = fma_(-a[tri(k, i)], x[k], s);
+    x[i] = s * a[tri(i, i)];
+  }
+}
+
+}  // namespace mpt
