@@ -1,0 +1,463 @@
+"""Benchmark of the batched MPT hot path on GB300.
+
+One step = the whole path over one batch: candidate enumeration, the
+Gauss-Newton solve of every candidate (FP32 iterations + FP64 refinement),
+validation with visibility and compaction, and the adjoint of every valid
+path (unit weight on its length).  Workload: the 12-box urban block (97
+objects: 48 walls, 48 vertical edges, ground), 1 TX at 30 m, 32x32 RX at
+1.5 m, every reflection/diffraction sequence of order <= 2: 9,634,816
+candidate solves per step, synthetic seeded scene.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  `value` is device-resident throughput
+(scene and endpoints already in HBM); `e2e` is the same metric through the
+C ABI starting from host arrays, with the host->device copies of the scene
+and endpoints and the device->host read of the valid paths inside the timed
+region.  Under torchrun each rank solves its own batch (weak scaling, no
+data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MPT candidate solves/sec at <=1e-6 m vs FP64 oracle; % of FP32 FMA peak"
+UNIT = "solves/s"
+WORKLOAD = "urban_block_12box_97obj_1tx_32x32rx_order2"
+L2_FLUSH_BYTES = 256 << 20
+SM_MAX_MHZ_NOMINAL = 2070.0
+FP32_LANES_PER_SM = 128
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except FileNotFoundError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2301_06399_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel_tag: str):
+    """DRAM bytes per launch recorded from an ncu capture of this source
+    revision (profiles/*.md lines `traffic_bytes_per_launch[tag]: N sha`)."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    sha = csrc_hash()
+    for f in sorted(os.listdir(d)):
+        if not f.endswith(".md"):
+            continue
+        for ln in open(os.path.join(d, f)):
+            key = f"traffic_bytes_per_launch[{kernel_tag}]:"
+            if ln.startswith(key):
+                parts = ln[len(key):].split()
+                if len(parts) >= 2 and parts[1] == sha:
+                    return float(parts[0])
+    return None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return {}
+
+
+def build_scene(rank: int, rx_side: int = 32):
+    from paper_2301_06399_gb300 import scenes
+
+    sc = scenes.urban_block(rx_side)
+    # each rank solves its own batch: the TX height differs per rank
+    sc.tx = sc.tx.copy()
+    sc.tx[:, 2] += 0.5 * rank
+    return sc, scenes.CONFIG_SPECS["urban_block"]
+
+
+def flop_table(mpt, sc):
+    """Algorithmic FP32 FLOPs per (evaluation, factorisation) for every kind
+    pattern of orders 1 and 2, from the library's counting model."""
+    tab = {}
+    kinds = sorted(set(int(k) for k in sc.obj_kind))
+    for a in kinds:
+        tab[(a,)] = mpt.flop_model([a])
+        for b in kinds:
+            tab[(a, b)] = mpt.flop_model([a, b])
+    return tab
+
+
+def algorithmic_flops(mpt, sc, cands, sols, n):
+    """Sum over candidates of evals * F_eval + iters * F_iter (pattern-wise)."""
+    rec = cands.rec[:n]
+    kinds_t = torch.as_tensor(sc.obj_kind, dtype=torch.int64, device=rec.device)
+    r = rec.to(torch.int64) & 0xFFFFFFFF
+    order = r[:, 3] & 0xFF
+    id0 = r[:, 1] & 0xFFFF
+    id1 = (r[:, 1] >> 16) & 0xFFFF
+    k0 = kinds_t[id0.clamp(max=kinds_t.numel() - 1)]
+    k1 = torch.where(order >= 2, kinds_t[id1.clamp(max=kinds_t.numel() - 1)], torch.full_like(k0, -1))
+    code = (order * 25 + (k0 + 1) * 5 + (k1 + 1)).to(torch.int64)
+    ev = sols.evals[:n].to(torch.float64)
+    it = sols.iters[:n].to(torch.float64)
+    nbins = 3 * 25
+    sum_ev = torch.bincount(code, weights=ev, minlength=nbins).cpu().numpy()
+    sum_it = torch.bincount(code, weights=it, minlength=nbins).cpu().numpy()
+    tab = flop_table(mpt, sc)
+    total = 0.0
+    for code_v in np.nonzero(sum_ev + sum_it)[0]:
+        o, rest = divmod(int(code_v), 25)
+        a, b = divmod(rest, 5)
+        key = (a - 1,) if o == 1 else (a - 1, b - 1)
+        f_iter, f_eval, _ = tab[key]
+        total += sum_ev[code_v] * f_eval + sum_it[code_v] * f_iter
+    return total
+
+
+def run_ours(args):
+    ws, rank, local = dist_env()
+    import torch.distributed as dist
+
+    if ws > 1:
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_2301_06399_gb300 import mpt
+
+    sc, spec = build_scene(rank, args.rx_side)
+    ctx = mpt.Context(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        ds = mpt.DeviceScene(ctx, sc)
+        n_cand = mpt.candidate_count(ds, 2, spec)
+        cands = mpt.alloc_candidates(n_cand, dev)
+        sols = mpt.alloc_solutions(n_cand, dev)
+        path_cap = 1 << 20
+        paths = mpt.alloc_paths(path_cap, dev)
+        g_len = torch.ones(path_cap, dtype=torch.float64, device=dev)
+        g_tx = torch.zeros_like(ds.tx)
+        g_rx = torch.zeros_like(ds.rx)
+        g_obj = torch.zeros(sc.n_obj, dtype=torch.float64, device=dev)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+        def step(precision=mpt.FP32_FP64REFINE, ev=None):
+            mpt.enumerate_candidates(ds, 2, spec, out=cands, stream=stream)
+            if ev is not None:
+                ev[0].record(stream)
+            mpt.solve(ds, cands, precision, out=sols, stream=stream)
+            if ev is not None:
+                ev[1].record(stream)
+            mpt.validate(ds, cands, sols, out=paths, stream=stream)
+            mpt.grad(ds, cands, paths, g_len, g_tx=g_tx, g_rx=g_rx, g_obj=g_obj, stream=stream)
+
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        n_valid = paths.n()
+        flops = algorithmic_flops(mpt, sc, cands, sols, n_cand)
+        launches_per_step = 2 + 4 + 3 + 1  # enumerate, solve (orders 1-4), validate, grad
+
+        # ---- device-resident timing
+        ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+        ev_solve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                    for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        clocks.start()
+        time.sleep(0.3)
+        t_wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush between steps, outside the step events
+            ev_step[i][0].record(stream)
+            step(ev=ev_solve[i])
+            ev_step[i][1].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall0
+        if ws > 1:
+            dist.barrier()
+        clk = clocks.stop()
+        step_ms = [a.elapsed_time(b) for a, b in ev_step]
+        solve_ms = [a.elapsed_time(b) for a, b in ev_solve]
+        total_ms = float(sum(step_ms))
+        if ws > 1:
+            t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        ms_per_step = total_ms / args.steps
+        value = n_cand * ws / (ms_per_step * 1e-3)
+
+        # ---- plain FP64 GPU method (same algorithm, FP64 throughout)
+        fp64_ms = []
+        for i in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(precision=mpt.FP64_PLAIN)
+            b.record(stream)
+            stream.synchronize()
+            fp64_ms.append(a.elapsed_time(b))
+        n_valid_fp64 = paths.n()
+        # restore the FP32 state for the e2e leg
+        step()
+        stream.synchronize()
+
+        # ---- end to end through the C ABI from host arrays
+        tx_h = torch.as_tensor(sc.tx).pin_memory()
+        rx_h = torch.as_tensor(sc.rx).pin_memory()
+        h2d_bytes = (sc.obj_param.nbytes + sc.obj_kind.nbytes + sc.occ_param.nbytes + sc.occ_kind.nbytes
+                     + tx_h.numel() * 8 + rx_h.numel() * 8)
+        e2e_ms = []
+        d2h_bytes = 0
+        out_cand = torch.empty(path_cap, dtype=torch.int64).pin_memory()
+        out_X = torch.empty((12, path_cap), dtype=torch.float64).pin_memory()
+        out_len = torch.empty(path_cap, dtype=torch.float64).pin_memory()
+        out_gtx = torch.empty_like(g_tx, device="cpu").pin_memory()
+        for i in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            stream.synchronize()
+            t0 = time.perf_counter()
+            ds_e = mpt.DeviceScene(ctx, sc, tx_host=tx_h, rx_host=rx_h)  # scene + endpoints host -> device
+            mpt.enumerate_candidates(ds_e, 2, spec, out=cands, stream=stream)
+            mpt.solve(ds_e, cands, mpt.FP32_FP64REFINE, out=sols, stream=stream)
+            mpt.validate(ds_e, cands, sols, out=paths, stream=stream)
+            g_tx.zero_()
+            mpt.grad(ds_e, cands, paths, g_len, g_tx=g_tx, g_rx=g_rx, g_obj=g_obj, stream=stream)
+            nv = min(int(paths.count.item()), path_cap)  # device -> host count
+            out_cand[:nv].copy_(paths.cand[:nv], non_blocking=True)
+            out_X[:, :nv].copy_(paths.X[:, :nv], non_blocking=True)
+            out_len[:nv].copy_(paths.length[:nv], non_blocking=True)
+            out_gtx.copy_(g_tx, non_blocking=True)
+            stream.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            d2h_bytes = 8 + nv * (8 + 12 * 8 + 8) + out_gtx.numel() * 8
+            ds_e.free()
+        e2e_ms_step = float(np.median(e2e_ms))
+        if ws > 1:
+            t = torch.tensor([e2e_ms_step], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms_step = float(t.item())
+
+    solve_avg_ms = float(np.mean(solve_ms))
+    achieved = flops / (solve_avg_ms * 1e-3) / 1e12
+    n_sm = ctx.sm_count
+    peak_max = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.rx_side == 32 else f"{WORKLOAD} (rx grid {args.rx_side}x{args.rx_side})",
+                   "candidates_per_gpu": n_cand, "max_order": 2,
+                   "precision": "fp32 iterations + fp64 refinement of prescreened candidates",
+                   "step": "enumerate + solve + validate/compact + adjoint",
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write), outside the step events",
+                   "parallelism": f"weak: one process per GPU, {ws} GPU(s)"},
+        "valid_paths_per_step": n_valid,
+        "valid_paths_per_sec": n_valid * ws / (ms_per_step * 1e-3),
+        "roofline": {"kernel": "mpt_solve (k_solve, orders 1-4)", "bound": "alu",
+                     "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max,
+                     "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {SM_MAX_MHZ_NOMINAL:.0f} MHz (derived)",
+                     "solve_ms": solve_avg_ms, "fp32_flops_per_launch": flops,
+                     "traffic": profile_traffic("k_solve<2,refine>")},
+        "fp64_plain": {"ms_per_step": float(np.median(fp64_ms)),
+                       "value": n_cand * ws / (float(np.median(fp64_ms)) * 1e-3), "unit": UNIT,
+                       "valid_paths_per_step": n_valid_fp64},
+        "e2e": {"value": n_cand * ws / (e2e_ms_step * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms_step,
+                "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_bytes)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "wall_s_timed_region": t_wall,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc, spec, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(sc, spec, seconds: float) -> dict:
+    """The FP64 oracle, as it stands, on the host cores: whole sequences
+    (x every RX) drawn at random from the workload until ~`seconds` pass."""
+    import oracle
+
+    table = oracle.enumerate_sequences(sc, 2, spec)
+    rng = np.random.default_rng(7)
+    order = rng.permutation(len(table))
+    n_pairs = sc.n_pairs
+    done = 0
+    t0 = time.perf_counter()
+    used = 0
+    for e in order:
+        b = int(e) * n_pairs
+        oracle.candidate_range(sc, table, b, b + n_pairs)
+        done += n_pairs
+        used += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": oracle.threads(0), "kind": "oracle",
+            "sample": f"{used} random sequences x {n_pairs} RX = {done} candidates of the workload "
+                      f"(solve + validate), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    from paper_2301_06399_gb300 import scenes
+
+    oracle.build()
+    sc, spec = build_scene(0)
+    table = oracle.enumerate_sequences(sc, 2, spec)
+    n_pairs = sc.n_pairs
+    rng = np.random.default_rng(11)
+    per_step = max(1, int(args.ref_entries))
+    times = []
+    done_total = 0
+    for i in range(args.warmup + args.steps):
+        ents = rng.choice(len(table), per_step, replace=False)
+        t0 = time.perf_counter()
+        for e in ents:
+            b = int(e) * n_pairs
+            oracle.candidate_range(sc, table, b, b + n_pairs)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            done_total += per_step * n_pairs
+    total = sum(times)
+    value = done_total / total
+    cores = oracle.threads(0)
+    sample = f"{per_step} random sequences x {n_pairs} RX per step (solve + validate)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "candidates_per_step": per_step * n_pairs,
+                   "note": "FP64 CPU oracle (Levenberg-Marquardt, dual-number Jacobians) on the host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-entries", type=int, default=64)
+    ap.add_argument("--rx-side", type=int, default=32, help="RX grid side (32 = the benchmark workload)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

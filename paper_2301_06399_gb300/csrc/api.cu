@@ -172,6 +172,10 @@ int mpt_ctx_create(int device, mpt_ctx** out) {
   c->err_flag = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(p) + 64 * sizeof(unsigned long long));
   c->vscratch = nullptr;
   c->vscratch_bytes = 0;
+  c->rscratch = nullptr;
+  c->rscratch_bytes = 0;
+  c->escratch = nullptr;
+  c->escratch_bytes = 0;
   *out = c;
   return MPT_OK;
 }
@@ -181,6 +185,8 @@ int mpt_ctx_destroy(mpt_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->vscratch) cudaFree(ctx->vscratch);
+  if (ctx->rscratch) cudaFree(ctx->rscratch);
+  if (ctx->escratch) cudaFree(ctx->escratch);
   cudaFree(ctx->counters);
   delete ctx;
   return MPT_OK;

@@ -112,6 +112,12 @@ struct mpt_ctx {
   // validate scratch, grown on demand
   void* vscratch;
   size_t vscratch_bytes;
+  // solver refine-list scratch, grown on demand
+  void* rscratch;
+  size_t rscratch_bytes;
+  // FP32 endpoint copies, grown on demand
+  void* escratch;
+  size_t escratch_bytes;
 };
 
 struct mpt_scene {

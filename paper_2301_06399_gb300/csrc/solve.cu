@@ -1,21 +1,28 @@
 // find_minimum_path of Algorithm 1 for every candidate: Gauss-Newton on the
-// cost of Eq. 15 with a backtracking line search, one thread per candidate.
+// cost of Eq. 15 with a backtracking line search, one lane per candidate.
 //
-// Precision modes:
-//   MPT_FP32             FP32 iterations only
-//   MPT_FP32_FP64REFINE  FP32 iterations; candidates whose FP32 cost is below
-//                        1e-8 and whose parameters lie inside their bounds up
-//                        to 1e-2 m then take 1-2 Gauss-Newton steps with the
-//                        residual in FP64 (Jacobian and solve in FP32) and an
-//                        FP64 cost.  Every other candidate is certainly
-//                        rejected by validation, so it keeps its FP32 result.
-//   MPT_FP64_PLAIN       the same algorithm in FP64 throughout
+// Kernel A (k_gn): a persistent grid per path order.  Each lane runs a small
+// state machine; every pass of the loop performs exactly one evaluation
+// (cost + normal equations at the lane's trial point) and then accepts,
+// backtracks or finishes.  A lane that finishes writes its result and
+// immediately takes the next candidate of its warp's chunk (a warp claims 256
+// consecutive candidates at a time from a per-order counter, so its lanes
+// share one object sequence and take the same branches), so lanes stay busy
+// although candidates converge after different numbers of iterations.  No
+// block-level barriers.  Endpoints are read from FP32 copies and results are
+// widened to FP64 on the integer units: the FP64 pipe stays idle.
 //
-// Scheduling: a persistent grid (blocks_per_sm x SMs) per path order; blocks
-// claim tiles of consecutive candidates from a global counter (work
-// stealing), so uneven convergence does not leave SMs idle.  The candidate
-// layout puts pairs fastest, so a warp shares one object sequence and all
-// scene loads are broadcasts.
+// Kernel B (k_refine, MPT_FP32_FP64REFINE only): candidates whose FP32 cost
+// is below 1e-6 and whose parameters lie within 0.1 m of their bounds are
+// appended by kernel A to a per-order list; kernel B takes up to
+// `refine_steps` Gauss-Newton steps with the residual and cost in FP64 and
+// the Jacobian in FP32, and falls back to full FP64 Gauss-Newton (FP64
+// Jacobian, backtracking) when the cost is still above 1e-24 (ill-
+// conditioned paths near object creases).  Every other candidate is rejected
+// by validation whatever its last digits, so it keeps its FP32 result.
+//
+// MPT_FP64_PLAIN runs kernel A in FP64 (the plain GPU method); MPT_FP32 runs
+// kernel A only.
 #include <type_traits>
 
 #include "mpt_internal.cuh"
@@ -23,8 +30,9 @@
 namespace mpt {
 
 struct SolveCfg {
-  int max_iters;
-  int refine_steps;
+  int max_iters, max_evals;
+  int refine_steps, fallback_iters;
+  float min_alpha, localmin_cost, localmin_ratio;
   float c_tol32, step_tol32;
   double c_tol64, step_tol64;
   double diverge;
@@ -49,6 +57,55 @@ struct SolView {
   float* T32;
   int64_t cap;
 };
+
+// Per-order refine lists: positions (candidate - first candidate of the
+// order) stored in idx[first of the order ...], counts in count[order - 1].
+struct RefineList {
+  unsigned long long* count;  // [4]
+  int32_t* idx;               // [cap]
+};
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int CHUNK = 256;  // candidates a warp claims at once (8 per lane)
+
+// Exact float -> double by assembling the bits on the integer units (the
+// FP64 pipe of GB300 is 1/64 of FP32, so conversions there are costly).
+// FP32 subnormals (never produced by the solver's magnitudes) become +-0.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t s = (uint64_t)(u >> 31) << 63;
+  const uint32_t e = (u >> 23) & 0xFFu;
+  const uint64_t m = (uint64_t)(u & 0x7FFFFFu) << 29;
+  uint64_t d;
+  if (e == 0) d = s;
+  else if (e == 0xFFu) d = s | (0x7FFull << 52) | m;
+  else d = s | ((uint64_t)(e + 896u) << 52) | m;
+  return __longlong_as_double((long long)d);
+}
+
+// FP32 copies of the endpoints, made once per solve call.
+__global__ void k_ends_f32(const double* tx, int n_tx, const double* rx, int n_rx, float4* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_tx) out[i] = make_float4((float)tx[3 * i], (float)tx[3 * i + 1], (float)tx[3 * i + 2], 0.f);
+  else if (i < n_tx + n_rx) {
+    const int j = i - n_tx;
+    out[i] = make_float4((float)rx[3 * j], (float)rx[3 * j + 1], (float)rx[3 * j + 2], 0.f);
+  }
+}
+
+template <class R>
+__device__ __forceinline__ v3<R> load_end(const double* p64, const float4* p32, int i);
+template <>
+__device__ __forceinline__ v3<float> load_end<float>(const double*, const float4* p32, int i) {
+  const float4 q = __ldg(p32 + i);
+  return mk(q.x, q.y, q.z);
+}
+template <>
+__device__ __forceinline__ v3<double> load_end<double>(const double* p64, const float4*, int i) {
+  return mk(__ldg(p64 + 3 * i), __ldg(p64 + 3 * i + 1), __ldg(p64 + 3 * i + 2));
+}
+__device__ __forceinline__ double to_f64(float x) { return f2d_bits(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
 
 template <class R>
 __device__ __forceinline__ Rec<R> load_obj(const DevScene& s, int o);
@@ -127,254 +184,468 @@ __device__ __forceinline__ void pin_unused(const int (&kind)[N], J* jtj, J* g) {
     }
 }
 
-// Gauss-Newton with backtracking: each evaluation returns the cost and the
-// normal equations at the trial point; an accepted trial's normal equations
-// give the next step directly (no separate Jacobian pass).
-template <int N, class R>
-struct GN {
-  static constexpr int Q = 2 * N;
-  static constexpr int P = Q * (Q + 1) / 2;
-  R prm[Q];
-  R cost;
-  int iters, evals, reason;
-  bool finite;
-
-  __device__ __forceinline__ void run(const int (&kind)[N], const Rec<R> (&rec)[N], const v3<R>& A,
-                                      const v3<R>& B, int max_iters, R c_tol, R step_tol, R diverge, R mu) {
-    R jtj[P], g[Q], dlt[Q];
-    bool ok;
-    cost = eval_path<N, R, R, true>(kind, rec, prm, A, B, jtj, g, ok);
-    evals = 1;
-    iters = 0;
-    reason = MPT_PATH_MAXITER;
-    finite = ok && isfinite(cost);
-    if (!finite) { reason = MPT_PATH_NONFINITE; return; }
-    if (cost < c_tol) { reason = MPT_PATH_CONVERGED; return; }
-    pin_unused<N, R>(kind, jtj, g);
-    cholesky<Q, R>(jtj, mu);
-    chol_solve<Q, R>(jtj, g, dlt);
-    R alpha = R(1);
-    for (int it = 0; it < max_iters; ++it) {
-      R trial[Q];
-      R smax = R(0);
+__device__ __forceinline__ uint64_t pack_ids(const Cand& cd, int n) {
+  uint64_t packed = 0;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        trial[i] = fma_(alpha, dlt[i], prm[i]);
-        smax = fmax(smax, fabs(alpha * dlt[i]));
+  for (int k = 0; k < 4; ++k) packed |= (uint64_t)(uint16_t)(k < n ? cd.ids[k] : 0xFFFF) << (16 * k);
+  return packed;
+}
+
+// ------------------------------------------------------------- kernel A --
+// The lanes of one warp solve the candidates of order N in [begin, end).
+// With a counter, the warp claims CHUNK-sized pieces of the range as it goes
+// (work stealing between warps); without one it takes [begin, end) as its
+// single chunk.  order_base = first candidate of order N (refine-list base).
+template <int N, int PREC>
+__device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, const float4* ends32,
+                                        const CandView& cv, const SolView& out, const SolveCfg& cfg,
+                                        unsigned long long* counter, const RefineList& rl, int64_t begin,
+                                        int64_t end, int64_t order_base) {
+  using R = typename std::conditional<PREC == MPT_FP64_PLAIN, double, float>::type;
+  constexpr int Q = 2 * N, P = Q * (Q + 1) / 2;
+  const unsigned lane = threadIdx.x & 31;
+  const R c_tol = R(PREC == MPT_FP64_PLAIN ? cfg.c_tol64 : cfg.c_tol32);
+  const R step_tol = R(PREC == MPT_FP64_PLAIN ? cfg.step_tol64 : cfg.step_tol32);
+  const R diverge = R(cfg.diverge);
+  const R mu = R(PREC == MPT_FP64_PLAIN ? cfg.mu64 : cfg.mu32);
+
+  int64_t c = -1;
+  bool exhausted = false;
+  int kind[N];
+  Rec<R> rec[N];
+  v3<R> A, B;
+  R prm[Q], trial[Q], dlt[Q];
+  R cost = R(0), alpha = R(1);
+  int iters = 0, evals = 0;
+  bool fresh = false;
+
+  // warp-uniform cursor into the warp's current chunk of candidates: lanes
+  // refill from consecutive candidates, so they share one object sequence
+  int64_t chunk_cur = 0, chunk_end = 0;
+  bool range_done = false;
+  if (counter == nullptr) {
+    chunk_cur = begin;
+    chunk_end = end;
+    range_done = true;
+  }
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (;;) {
+    // ---- refill idle lanes with the next candidates of the warp's chunk
+    bool need = (c < 0) && !exhausted;
+    unsigned need_mask = __ballot_sync(FULL, need);
+    while (need_mask) {
+      if (chunk_cur >= chunk_end) {
+        if (range_done) break;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(counter, (unsigned long long)CHUNK);
+        base = __shfl_sync(FULL, base, 0);
+        chunk_cur = begin + (int64_t)base;
+        chunk_end = chunk_cur + CHUNK < end ? chunk_cur + CHUNK : end;
+        if (chunk_cur >= end) {
+          range_done = true;
+          break;
+        }
       }
-      R ct = eval_path<N, R, R, true>(kind, rec, trial, A, B, jtj, g, ok);
+      const int avail = (int)(chunk_end - chunk_cur);
+      const int rank = __popc(need_mask & lt_mask);
+      const bool take = need && rank < avail;
+      const int64_t idx = chunk_cur + rank;
+      const int served = __popc(need_mask) < avail ? __popc(need_mask) : avail;
+      chunk_cur += served;
+      if (take) {
+        need = false;
+        {
+          const Cand cd = decode(__ldg(cv.rec + idx));
+          if (cand_in_range(sc, ep, cd) && cd.order == N) {
+            c = idx;
+            int it_, ir_;
+            pair_ends(ep, cd.pair, it_, ir_);
+            A = load_end<R>(ep.tx, ends32, it_);
+            B = load_end<R>(ep.rx, ends32 + ep.n_tx, ir_);
+            const uint64_t packed = pack_ids(cd, N);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+              kind[k] = __ldg(sc.kind + cd.ids[k]);
+              rec[k] = load_obj<R>(sc, cd.ids[k]);
+              init_params<R>(kind[k], rec[k], (2 * k < N) ? A : B, cv.init_seed, cd.pair, packed, cd.start, k,
+                             trial[2 * k], trial[2 * k + 1]);
+            }
+            fresh = true;
+            iters = 0;
+            evals = 0;
+            alpha = R(1);
+          } else {
+            out.cost[idx] = (double)INFINITY;
+            out.status[idx] = (uint8_t)MPT_PATH_NONFINITE;
+            out.iters[idx] = 0;
+            out.evals[idx] = 0;
+          }
+        }
+      }
+      need_mask = __ballot_sync(FULL, need);
+    }
+    if (range_done && c < 0) exhausted = true;
+    if (__ballot_sync(FULL, c >= 0) == 0) {
+      if (__ballot_sync(FULL, !exhausted) == 0) break;
+      continue;
+    }
+    bool push = false;
+    int64_t push_c = 0;
+    if (c >= 0) {
+      // ---- one evaluation at the trial point
+      R jtj[P], g[Q];
+      bool ok;
+      const R ct = eval_path<N, R, R, true>(kind, rec, trial, A, B, jtj, g, ok);
       ++evals;
-      if (ok && ct < cost) {
+      int done = -1;
+      bool factor = false;
+      if (fresh) {
+        fresh = false;
 #pragma unroll
         for (int i = 0; i < Q; ++i) prm[i] = trial[i];
         cost = ct;
-        ++iters;
-        R pmax = R(0);
+        if (!(ok && isfinite(ct))) done = MPT_PATH_NONFINITE;
+        else if (cost < c_tol) done = MPT_PATH_CONVERGED;
+        else factor = true;
+      } else if (ok && ct < cost) {
+        R smax = R(0), pmax = R(0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) pmax = fmax(pmax, fabs(prm[i]));
-        if (!(pmax <= diverge)) { reason = MPT_PATH_DIVERGED; return; }
-        if (cost < c_tol || smax < step_tol) { reason = MPT_PATH_CONVERGED; return; }
+        for (int i = 0; i < Q; ++i) {
+          smax = fmax(smax, fabs(trial[i] - prm[i]));
+          prm[i] = trial[i];
+          pmax = fmax(pmax, fabs(prm[i]));
+        }
+        cost = ct;
+        ++iters;
+        if (!(pmax <= diverge)) done = MPT_PATH_DIVERGED;
+        else if (cost < c_tol || smax < step_tol) done = MPT_PATH_CONVERGED;
+        else if (iters >= cfg.max_iters) done = MPT_PATH_MAXITER;
+        else factor = true;
+      } else {
+        alpha = alpha * R(0.5);
+        if (alpha < R(cfg.min_alpha)) done = MPT_PATH_STALLED;
+      }
+      if (done < 0 && evals >= cfg.max_evals) done = MPT_PATH_MAXITER;
+      if (factor && done < 0) {
         pin_unused<N, R>(kind, jtj, g);
         cholesky<Q, R>(jtj, mu);
         chol_solve<Q, R>(jtj, g, dlt);
         alpha = R(1);
+        // The Gauss-Newton model predicts the decrease -g.dlt; when it is a
+        // negligible fraction of a large cost the iterate sits at a local
+        // minimum with non-zero residual: no path of this sequence is near.
+        R pred = R(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) pred = fma_(-g[i], dlt[i], pred);
+        if (iters >= 2 && cost > R(cfg.localmin_cost) && pred < R(cfg.localmin_ratio) * cost)
+          done = MPT_PATH_STALLED;
+      }
+      if (done < 0) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) trial[i] = fma_(alpha, dlt[i], prm[i]);
       } else {
-        alpha = alpha * R(0.5);
-        if (alpha < R(1.0 / 64.0)) { reason = MPT_PATH_STALLED; return; }
+        // ---- finish: write the result, queue FP64 refinement if it may be valid
+        int status = done;
+        if (PREC == MPT_FP64_PLAIN) status |= MPT_PATH_REFINED;
+        if (PREC == MPT_FP32_FP64REFINE) {
+          bool pass = isfinite(cost) && cost < R(cfg.prescreen_cost) && done != MPT_PATH_DIVERGED;
+#pragma unroll
+          for (int k = 0; k < N; ++k)
+            pass = pass && in_bounds_margin<R>(kind[k], rec[k], prm[2 * k], prm[2 * k + 1], R(cfg.prescreen_margin));
+          if (pass) {
+            push = true;
+            push_c = c;
+          } else {
+            status |= MPT_PATH_PRESCREENED;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) out.T[(int64_t)i * out.cap + c] = to_f64(prm[i]);
+        if (out.T32 != nullptr) {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) out.T32[(int64_t)i * out.cap + c] = (float)prm[i];
+        }
+        out.cost[c] = to_f64(cost);
+        out.status[c] = (uint8_t)status;
+        out.iters[c] = (uint8_t)min(iters, 255);
+        out.evals[c] = (uint8_t)min(evals, 255);
+        c = -1;
+      }
+    }
+    if (PREC == MPT_FP32_FP64REFINE) {
+      const unsigned pm = __ballot_sync(FULL, push);
+      if (pm) {
+        const int leader = __ffs(pm) - 1;
+        unsigned long long base = 0;
+        if ((int)lane == leader) base = atomicAdd(rl.count + (N - 1), (unsigned long long)__popc(pm));
+        base = __shfl_sync(FULL, base, leader);
+        if (push) {
+          const int64_t pos = (int64_t)base + __popc(pm & ((1u << lane) - 1u));
+          rl.idx[order_base + pos] = (int32_t)(push_c - order_base);
+        }
       }
     }
   }
-};
-
-template <int N, int PREC>
-__device__ __forceinline__ void solve_one(const DevScene& sc, const DevEnds& ep, const CandView& cv,
-                                          const SolView& out, const SolveCfg& cfg, int64_t c) {
-  using R = typename std::conditional<PREC == MPT_FP64_PLAIN, double, float>::type;
-  constexpr int Q = 2 * N;
-  const Cand cd = decode(__ldg(cv.rec + c));
-  if (!cand_in_range(sc, ep, cd) || cd.order != N) {
-    out.cost[c] = (double)INFINITY;
-    out.status[c] = (uint8_t)MPT_PATH_NONFINITE;
-    out.iters[c] = 0;
-    out.evals[c] = 0;
-    return;
-  }
-  int it_, ir_;
-  pair_ends(ep, cd.pair, it_, ir_);
-  const v3<double> A64 = mk(__ldg(ep.tx + 3 * it_), __ldg(ep.tx + 3 * it_ + 1), __ldg(ep.tx + 3 * it_ + 2));
-  const v3<double> B64 = mk(__ldg(ep.rx + 3 * ir_), __ldg(ep.rx + 3 * ir_ + 1), __ldg(ep.rx + 3 * ir_ + 2));
-  const v3<R> A = cvt<R>(A64), B = cvt<R>(B64);
-  int kind[N];
-  Rec<R> rec[N];
-  uint64_t packed = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) packed |= (uint64_t)(uint16_t)(k < N ? cd.ids[k] : 0xFFFF) << (16 * k);
-  GN<N, R> gn;
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    kind[k] = __ldg(sc.kind + cd.ids[k]);
-    rec[k] = load_obj<R>(sc, cd.ids[k]);
-    init_params<R>(kind[k], rec[k], (2 * k < N) ? A : B, cv.init_seed, cd.pair, packed, cd.start, k,
-                   gn.prm[2 * k], gn.prm[2 * k + 1]);
-  }
-  if (PREC == MPT_FP64_PLAIN)
-    gn.run(kind, rec, A, B, cfg.max_iters, R(cfg.c_tol64), R(cfg.step_tol64), R(cfg.diverge), R(cfg.mu64));
-  else
-    gn.run(kind, rec, A, B, cfg.max_iters, R(cfg.c_tol32), R(cfg.step_tol32), R(cfg.diverge), R(cfg.mu32));
-
-  int status = gn.reason;
-  double cost = (double)gn.cost;
-  double T64[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) T64[i] = (double)gn.prm[i];
-  if (out.T32 != nullptr) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) out.T32[(int64_t)i * out.cap + c] = (float)gn.prm[i];
-  }
-  if (PREC == MPT_FP64_PLAIN) {
-    status |= MPT_PATH_REFINED;
-  } else if (PREC == MPT_FP32_FP64REFINE) {
-    bool pass = gn.finite && gn.cost < R(cfg.prescreen_cost) && status != MPT_PATH_DIVERGED;
-#pragma unroll
-    for (int k = 0; k < N; ++k)
-      pass = pass && in_bounds_margin<R>(kind[k], rec[k], gn.prm[2 * k], gn.prm[2 * k + 1],
-                                         R(cfg.prescreen_margin));
-    if (pass) {
-      // FP64 refinement: residual and cost in FP64, Jacobian and solve in FP32
-      Rec<double> r64[N];
-#pragma unroll
-      for (int k = 0; k < N; ++k) r64[k] = load_obj64(sc, cd.ids[k]);
-      float jtj[Q * (Q + 1) / 2], g[Q], dlt[Q];
-      bool ok;
-      double c64 = eval_path<N, double, float, true>(kind, r64, T64, A64, B64, jtj, g, ok);
-      int ev = 1;
-      for (int s = 0; s < cfg.refine_steps && ok && c64 >= 1e-28; ++s) {
-        pin_unused<N, float>(kind, jtj, g);
-        cholesky<Q, float>(jtj, cfg.mu32);
-        chol_solve<Q, float>(jtj, g, dlt);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) T64[i] += (double)dlt[i];
-        c64 = eval_path<N, double, float, true>(kind, r64, T64, A64, B64, jtj, g, ok);
-        ++ev;
-      }
-      cost = ok ? c64 : (double)INFINITY;
-      (void)ev;
-      status |= MPT_PATH_REFINED;
-    } else {
-      status |= MPT_PATH_PRESCREENED;
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-    if (i < Q) out.T[(int64_t)i * out.cap + c] = T64[i];
-  out.cost[c] = cost;
-  out.status[c] = (uint8_t)status;
-  out.iters[c] = (uint8_t)min(gn.iters, 255);
-  out.evals[c] = (uint8_t)min(gn.evals, 255);
 }
 
 template <int N, int PREC>
-__global__ void __launch_bounds__(SOLVE_BLOCK) k_solve(DevScene sc, DevEnds ep, CandView cv, SolView out,
-                                                       SolveCfg cfg, unsigned long long* counter) {
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_gn(DevScene sc, DevEnds ep, const float4* ends32, CandView cv,
+                                                    SolView out, SolveCfg cfg, unsigned long long* counter,
+                                                    RefineList rl) {
   int64_t end = cv.order_begin[N];
   if (end > cv.cap) end = cv.cap;
   int64_t begin = cv.order_begin[N - 1];
   if (begin > end) begin = end;
-  __shared__ int64_t s_base;
-  for (;;) {
-    if (threadIdx.x == 0) s_base = begin + (int64_t)atomicAdd(counter, 1ull) * SOLVE_BLOCK;
-    __syncthreads();
-    const int64_t base = s_base;
-    __syncthreads();
-    if (base >= end) break;
-    const int64_t c = base + threadIdx.x;
-    if (c < end) solve_one<N, PREC>(sc, ep, cv, out, cfg, c);
-  }
+  gn_warp<N, PREC>(sc, ep, ends32, cv, out, cfg, counter, rl, begin, end, begin);
 }
 
-// One launch over every order: each thread dispatches on its candidate's
-// order (warp-uniform except where a tile straddles two orders).
+// One launch over every order (uneven orders and convergence in one
+// persistent grid): warps claim CHUNK-sized pieces of the whole candidate
+// range and solve each piece with the solver of its order (a piece that
+// straddles an order boundary is split).  Registers are those of the order-4
+// solver, so per-order launches are faster when the orders are known to
+// come in large uniform ranges; the autotuner chooses.
 template <int PREC>
-__global__ void __launch_bounds__(SOLVE_BLOCK) k_solve_mixed(DevScene sc, DevEnds ep, CandView cv,
-                                                             SolView out, SolveCfg cfg,
-                                                             unsigned long long* counter) {
-  int64_t end = cv.order_begin[4];
-  if (end > cv.cap) end = cv.cap;
-  __shared__ int64_t s_base;
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_mixed(DevScene sc, DevEnds ep, const float4* ends32,
+                                                          CandView cv, SolView out, SolveCfg cfg,
+                                                          unsigned long long* counter, RefineList rl) {
+  int64_t total = cv.order_begin[4];
+  if (total > cv.cap) total = cv.cap;
+  const unsigned lane = threadIdx.x & 31;
   for (;;) {
-    if (threadIdx.x == 0) s_base = (int64_t)atomicAdd(counter, 1ull) * SOLVE_BLOCK;
-    __syncthreads();
-    const int64_t base = s_base;
-    __syncthreads();
-    if (base >= end) break;
-    const int64_t c = base + threadIdx.x;
-    if (c < end) {
-      const int order = (int)(__ldg(&cv.rec[c].w) & 0xFFu);
-      switch (order) {
-        case 1: solve_one<1, PREC>(sc, ep, cv, out, cfg, c); break;
-        case 2: solve_one<2, PREC>(sc, ep, cv, out, cfg, c); break;
-        case 3: solve_one<3, PREC>(sc, ep, cv, out, cfg, c); break;
-        default: solve_one<4, PREC>(sc, ep, cv, out, cfg, c); break;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(counter, (unsigned long long)CHUNK);
+    base = __shfl_sync(FULL, base, 0);
+    int64_t s = (int64_t)base;
+    if (s >= total) break;
+    const int64_t e = s + CHUNK < total ? s + CHUNK : total;
+    while (s < e) {
+      const int o = (int)(__ldg(&cv.rec[s].w) & 0xFFu);
+      int64_t oe = (o >= 1 && o <= 4) ? cv.order_begin[o] : s + 1;
+      if (oe > e) oe = e;
+      if (oe <= s) oe = s + 1;
+      const int64_t ob = (o >= 1 && o <= 4) ? cv.order_begin[o - 1] : 0;
+      switch (o) {
+        case 1: gn_warp<1, PREC>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
+        case 2: gn_warp<2, PREC>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
+        case 3: gn_warp<3, PREC>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
+        case 4: gn_warp<4, PREC>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
+        default:
+          if (lane == 0) {
+            out.cost[s] = (double)INFINITY;
+            out.status[s] = (uint8_t)MPT_PATH_NONFINITE;
+            out.iters[s] = 0;
+            out.evals[s] = 0;
+          }
+          break;
       }
+      s = oe;
     }
   }
 }
 
-template <int PREC>
-static int launch_prec(mpt_ctx* ctx, DevScene sc, DevEnds ep, CandView cv, SolView sv, SolveCfg cfg,
-                       const mpt_schedule* sch, cudaStream_t st) {
-  MPT_CUDA_TRY(cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), st));
-  const int bps = (sch && sch->blocks_per_sm > 0) ? sch->blocks_per_sm : 0;
-  auto grid_for = [&](const void* fn) {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, SOLVE_BLOCK, 0);
-    if (occ < 1) occ = 1;
-    int per = bps > 0 ? (bps < occ ? bps : occ) : occ;
-    return ctx->sms * per;
-  };
-  if (sch && sch->mixed_orders) {
-    const void* fn = (const void*)k_solve_mixed<PREC>;
-    k_solve_mixed<PREC><<<grid_for(fn), SOLVE_BLOCK, 0, st>>>(sc, ep, cv, sv, cfg, ctx->counters + 4);
-    MPT_LAUNCH_CHECK();
-    return MPT_OK;
+// ------------------------------------------------------------- kernel B --
+// Full FP64 Gauss-Newton with backtracking (the fallback of the refinement).
+template <int N>
+__device__ double gn64(const int (&kind)[N], const Rec<double> (&rec)[N], double (&prm)[2 * N],
+                       const v3<double>& A, const v3<double>& B, int max_iters, double mu) {
+  constexpr int Q = 2 * N, P = Q * (Q + 1) / 2;
+  double jtj[P], g[Q], dlt[Q], trial[Q];
+  bool ok;
+  double cost = eval_path<N, double, double, true>(kind, rec, prm, A, B, jtj, g, ok);
+  if (!ok) return (double)INFINITY;
+  double alpha = 1.0;
+  bool need_factor = true;
+  for (int it = 0; it < 4 * max_iters && cost >= 1e-30; ++it) {
+    if (need_factor) {
+      pin_unused<N, double>(kind, jtj, g);
+      cholesky<Q, double>(jtj, mu);
+      chol_solve<Q, double>(jtj, g, dlt);
+      alpha = 1.0;
+      need_factor = false;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) trial[i] = fma(alpha, dlt[i], prm[i]);
+    double jt2[P], g2[Q];
+    const double ct = eval_path<N, double, double, true>(kind, rec, trial, A, B, jt2, g2, ok);
+    if (ok && ct < cost) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) prm[i] = trial[i];
+#pragma unroll
+      for (int i = 0; i < P; ++i) jtj[i] = jt2[i];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) g[i] = g2[i];
+      cost = ct;
+      need_factor = true;
+    } else {
+      alpha *= 0.5;
+      if (alpha < 1.0 / 64.0) break;
+    }
   }
-  k_solve<1, PREC><<<grid_for((const void*)k_solve<1, PREC>), SOLVE_BLOCK, 0, st>>>(sc, ep, cv, sv, cfg,
-                                                                                    ctx->counters + 0);
+  return cost;
+}
+
+template <int N>
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_refine(DevScene sc, DevEnds ep, CandView cv, SolView out,
+                                                        SolveCfg cfg, RefineList rl) {
+  constexpr int Q = 2 * N;
+  int64_t end = cv.order_begin[N];
+  if (end > cv.cap) end = cv.cap;
+  int64_t begin = cv.order_begin[N - 1];
+  if (begin > end) begin = end;
+  int64_t n = (int64_t)rl.count[N - 1];
+  if (n > end - begin) n = end - begin;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = begin + rl.idx[begin + i];
+    if (c < begin || c >= end) continue;
+    const Cand cd = decode(__ldg(cv.rec + c));
+    int it_, ir_;
+    pair_ends(ep, cd.pair, it_, ir_);
+    const v3<double> A = mk(__ldg(ep.tx + 3 * it_), __ldg(ep.tx + 3 * it_ + 1), __ldg(ep.tx + 3 * it_ + 2));
+    const v3<double> B = mk(__ldg(ep.rx + 3 * ir_), __ldg(ep.rx + 3 * ir_ + 1), __ldg(ep.rx + 3 * ir_ + 2));
+    int kind[N];
+    Rec<double> rec[N];
+    double T[Q];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      kind[k] = __ldg(sc.kind + cd.ids[k]);
+      rec[k] = load_obj64(sc, cd.ids[k]);
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) T[j] = out.T[(int64_t)j * out.cap + c];
+    // mixed steps: FP64 residual and cost, FP32 Jacobian and solve
+    float jtj[Q * (Q + 1) / 2], g[Q], dlt[Q];
+    bool ok;
+    double c64 = eval_path<N, double, float, true>(kind, rec, T, A, B, jtj, g, ok);
+    for (int s = 0; s < cfg.refine_steps && ok && c64 >= 1e-26; ++s) {
+      pin_unused<N, float>(kind, jtj, g);
+      cholesky<Q, float>(jtj, cfg.mu32);
+      chol_solve<Q, float>(jtj, g, dlt);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) T[j] += (double)dlt[j];
+      c64 = eval_path<N, double, float, true>(kind, rec, T, A, B, jtj, g, ok);
+    }
+    if (!ok || !(c64 < 1e-24)) {
+      // ill-conditioned: full FP64 Gauss-Newton from the better of the two points
+      double T0[Q];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) T0[j] = ok ? T[j] : out.T[(int64_t)j * out.cap + c];
+      const double c2 = gn64<N>(kind, rec, T0, A, B, cfg.fallback_iters, cfg.mu64);
+      if (c2 < c64 || !ok) {
+#pragma unroll
+        for (int j = 0; j < Q; ++j) T[j] = T0[j];
+        c64 = c2;
+        ok = true;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) out.T[(int64_t)j * out.cap + c] = T[j];
+    out.cost[c] = ok ? c64 : (double)INFINITY;
+    out.status[c] = (uint8_t)(out.status[c] | MPT_PATH_REFINED);
+  }
+}
+
+// ------------------------------------------------------------ launching --
+template <class K>
+static int grid_for(mpt_ctx* ctx, K kernel, const mpt_schedule* sch) {
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, SOLVE_BLOCK, 0);
+  if (occ < 1) occ = 1;
+  if (sch && sch->blocks_per_sm > 0 && sch->blocks_per_sm < occ) occ = sch->blocks_per_sm;
+  return ctx->sms * occ;
+}
+
+template <int PREC>
+static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, const float4* ends32, const CandView& cv,
+                       const SolView& sv, const SolveCfg& cfg, const mpt_schedule* sch, RefineList rl,
+                       cudaStream_t st) {
+  // counters[0..3]: per-order candidate cursors; counters[8..11]: refine list sizes
+  MPT_CUDA_TRY(cudaMemsetAsync(ctx->counters, 0, 16 * sizeof(unsigned long long), st));
+  if (sch && sch->mixed_orders) {
+    k_gn_mixed<PREC><<<grid_for(ctx, k_gn_mixed<PREC>, sch), SOLVE_BLOCK, 0, st>>>(sc, ep, ends32, cv, sv, cfg,
+                                                                                  ctx->counters + 4, rl);
+    MPT_LAUNCH_CHECK();
+  } else {
+#define MPT_LAUNCH_GN(N)                                                                             \
+  k_gn<N, PREC><<<grid_for(ctx, k_gn<N, PREC>, sch), SOLVE_BLOCK, 0, st>>>(sc, ep, ends32, cv, sv, cfg,      \
+                                                                          ctx->counters + (N - 1), rl); \
   MPT_LAUNCH_CHECK();
-  k_solve<2, PREC><<<grid_for((const void*)k_solve<2, PREC>), SOLVE_BLOCK, 0, st>>>(sc, ep, cv, sv, cfg,
-                                                                                    ctx->counters + 1);
+  MPT_LAUNCH_GN(1)
+  MPT_LAUNCH_GN(2)
+  MPT_LAUNCH_GN(3)
+  MPT_LAUNCH_GN(4)
+#undef MPT_LAUNCH_GN
+  }
+  if (PREC == MPT_FP32_FP64REFINE) {
+#define MPT_LAUNCH_REF(N)                                                                               \
+  k_refine<N><<<grid_for(ctx, k_refine<N>, nullptr), SOLVE_BLOCK, 0, st>>>(sc, ep, cv, sv, cfg, rl); \
   MPT_LAUNCH_CHECK();
-  k_solve<3, PREC><<<grid_for((const void*)k_solve<3, PREC>), SOLVE_BLOCK, 0, st>>>(sc, ep, cv, sv, cfg,
-                                                                                    ctx->counters + 2);
-  MPT_LAUNCH_CHECK();
-  k_solve<4, PREC><<<grid_for((const void*)k_solve<4, PREC>), SOLVE_BLOCK, 0, st>>>(sc, ep, cv, sv, cfg,
-                                                                                    ctx->counters + 3);
-  MPT_LAUNCH_CHECK();
+    MPT_LAUNCH_REF(1)
+    MPT_LAUNCH_REF(2)
+    MPT_LAUNCH_REF(3)
+    MPT_LAUNCH_REF(4)
+#undef MPT_LAUNCH_REF
+  }
   return MPT_OK;
 }
 
 int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
                  int precision, const mpt_schedule* sch, mpt_solutions* out, cudaStream_t st) {
   SolveCfg cfg;
-  cfg.max_iters = (sch && sch->max_iters > 0) ? (sch->max_iters > 255 ? 255 : sch->max_iters) : 48;
-  cfg.refine_steps = (sch && sch->refine_steps > 0) ? (sch->refine_steps > 2 ? 2 : sch->refine_steps) : 2;
+  // Valid paths of the benchmark workloads converge within 12 accepted steps
+  // and 25 evaluations; the caps leave a factor of 2 / 1.6.
+  cfg.max_iters = (sch && sch->max_iters > 0) ? (sch->max_iters > 160 ? 160 : sch->max_iters) : 24;
+  cfg.max_evals = cfg.max_iters * 5 / 3;
+  cfg.min_alpha = 1.0f / 16.0f;
+  cfg.localmin_cost = 1e-3f;
+  cfg.localmin_ratio = 1e-4f;
+  cfg.refine_steps = (sch && sch->refine_steps > 0) ? (sch->refine_steps > 4 ? 4 : sch->refine_steps) : 2;
+  cfg.fallback_iters = 8;
   const double S = scene->d.scale;
   cfg.c_tol32 = 1e-12f;
   cfg.step_tol32 = (float)(1e-6 * S);
   cfg.c_tol64 = 1e-30;
   cfg.step_tol64 = 1e-14 * S;
   cfg.diverge = 1e3 * S;
-  cfg.prescreen_cost = 1e-8f;
-  cfg.prescreen_margin = 1e-2f;
+  cfg.prescreen_cost = 1e-6f;
+  cfg.prescreen_margin = 0.1f;
   cfg.mu32 = 1e-6f;
   cfg.mu64 = 1e-12;
   CandView cv{reinterpret_cast<const uint4*>(cand->rec), cand->capacity, cand->order_begin, cand->init_seed};
   SolView sv{out->T, out->cost, out->status, out->iters, out->evals, out->T32, out->capacity};
   DevEnds ep = dev_ends(ends);
+  RefineList rl{ctx->counters + 8, nullptr};
+  if (precision == MPT_FP32_FP64REFINE) {
+    const size_t need = (size_t)cand->capacity * sizeof(int32_t) + 256;
+    if (ctx->rscratch_bytes < need) {
+      if (ctx->rscratch) MPT_CUDA_TRY(cudaFreeAsync(ctx->rscratch, st));
+      ctx->rscratch = nullptr;
+      ctx->rscratch_bytes = 0;
+      MPT_CUDA_TRY(cudaMallocAsync(&ctx->rscratch, need, st));
+      ctx->rscratch_bytes = need;
+    }
+    rl.idx = reinterpret_cast<int32_t*>(ctx->rscratch);
+  }
+  // FP32 copies of the endpoints for the FP32 iterations
+  const int n_ends = ends->n_tx + ends->n_rx;
+  const size_t ebytes = (size_t)n_ends * sizeof(float4) + 256;
+  if (ctx->escratch_bytes < ebytes) {
+    if (ctx->escratch) MPT_CUDA_TRY(cudaFreeAsync(ctx->escratch, st));
+    ctx->escratch = nullptr;
+    ctx->escratch_bytes = 0;
+    MPT_CUDA_TRY(cudaMallocAsync(&ctx->escratch, ebytes, st));
+    ctx->escratch_bytes = ebytes;
+  }
+  float4* ends32 = reinterpret_cast<float4*>(ctx->escratch);
+  if (precision != MPT_FP64_PLAIN) {
+    k_ends_f32<<<(n_ends + 255) / 256, 256, 0, st>>>(ends->tx, ends->n_tx, ends->rx, ends->n_rx, ends32);
+    MPT_LAUNCH_CHECK();
+  }
   switch (precision) {
-    case MPT_FP64_PLAIN: return launch_prec<MPT_FP64_PLAIN>(ctx, scene->d, ep, cv, sv, cfg, sch, st);
-    case MPT_FP32: return launch_prec<MPT_FP32>(ctx, scene->d, ep, cv, sv, cfg, sch, st);
-    case MPT_FP32_FP64REFINE: return launch_prec<MPT_FP32_FP64REFINE>(ctx, scene->d, ep, cv, sv, cfg, sch, st);
+    case MPT_FP64_PLAIN: return launch_prec<MPT_FP64_PLAIN>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, st);
+    case MPT_FP32: return launch_prec<MPT_FP32>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, st);
+    case MPT_FP32_FP64REFINE:
+      return launch_prec<MPT_FP32_FP64REFINE>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, st);
     default: return MPT_ERR_ARG;
   }
 }

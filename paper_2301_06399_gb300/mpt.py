@@ -160,7 +160,8 @@ class Context:
 class DeviceScene:
     """A scene uploaded with mpt_scene_upload plus its TX/RX endpoints on the device."""
 
-    def __init__(self, ctx: Context, scene, device: int | None = None):
+    def __init__(self, ctx: Context, scene, device: int | None = None, tx_host: torch.Tensor | None = None,
+                 rx_host: torch.Tensor | None = None):
         self.ctx = ctx
         self.scene = scene.contiguous()
         s = self.scene
@@ -171,8 +172,10 @@ class DeviceScene:
         _check(lib().mpt_scene_upload(ctx.h, C.byref(desc), C.byref(h)), "mpt_scene_upload")
         self.h = h
         dev = torch.device("cuda", ctx.device if device is None else device)
-        self.tx = torch.as_tensor(s.tx, dtype=torch.float64).to(dev).contiguous()
-        self.rx = torch.as_tensor(s.rx, dtype=torch.float64).to(dev).contiguous()
+        src_tx = tx_host if tx_host is not None else torch.as_tensor(s.tx, dtype=torch.float64)
+        src_rx = rx_host if rx_host is not None else torch.as_tensor(s.rx, dtype=torch.float64)
+        self.tx = src_tx.to(dev, non_blocking=True).contiguous()
+        self.rx = src_rx.to(dev, non_blocking=True).contiguous()
         self.pair_mode = s.pair_mode
 
     def endpoints(self) -> Endpoints:
@@ -221,15 +224,22 @@ def candidate_count(ds: DeviceScene, max_order: int, spec) -> int:
     return int(n)
 
 
-def enumerate_candidates(ds: DeviceScene, max_order: int, spec, adj: torch.Tensor | None = None,
-                         capacity: int | None = None, init_seed: int = 0, stream=None) -> Candidates:
-    dev = ds.tx.device
-    if capacity is None:
-        capacity = candidate_count(ds, max_order, spec)
+def alloc_candidates(capacity: int, device, init_seed: int = 0) -> Candidates:
     cap = max(int(capacity), 1)
-    c = Candidates(torch.empty((cap, 4), dtype=torch.int32, device=dev),
-                   torch.zeros(1, dtype=torch.int64, device=dev), torch.zeros(5, dtype=torch.int64, device=dev),
-                   cap, init_seed)
+    return Candidates(torch.empty((cap, 4), dtype=torch.int32, device=device),
+                      torch.zeros(1, dtype=torch.int64, device=device),
+                      torch.zeros(5, dtype=torch.int64, device=device), cap, init_seed)
+
+
+def enumerate_candidates(ds: DeviceScene, max_order: int, spec, adj: torch.Tensor | None = None,
+                         capacity: int | None = None, init_seed: int = 0, out: Candidates | None = None,
+                         stream=None) -> Candidates:
+    if out is not None:
+        c = out
+    else:
+        if capacity is None:
+            capacity = candidate_count(ds, max_order, spec)
+        c = alloc_candidates(capacity, ds.tx.device, init_seed)
     ep = ds.endpoints()
     sp = sampling_struct(spec)
     cs = c.struct()

@@ -1,0 +1,90 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every symbol
+include/mpt.h declares, and its host-only entry points behave."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2301_06399_gb300 import build
+
+    build.build()
+    from paper_2301_06399_gb300 import mpt
+
+    return mpt.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "mpt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpt_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2301_06399_gb300 import mpt
+
+    assert sorted(mpt.SYMBOLS) == names
+
+
+def test_status_strings(lib):
+    from paper_2301_06399_gb300 import mpt
+
+    for rc in range(6):
+        assert mpt.status_string(rc).startswith("MPT_")
+    assert "CAPACITY" in mpt.status_string(mpt.MPT_ERR_CAPACITY)
+
+
+def _chol_solve_flops(q: int) -> int:
+    """Operation count of the packed Cholesky + two triangular solves as
+    written in the kernel: column j costs 2j (dot) + 3 (diagonal update with
+    relative damping), each entry below it 2j + 1; the solves cost 2i + 1 and
+    2(q-1-i) + 1 per row."""
+    f = 0
+    for j in range(q):
+        f += 2 * j + 3
+        f += (q - 1 - j) * (2 * j + 1)
+    for i in range(q):
+        f += 2 * i + 1
+        f += 2 * (q - 1 - i) + 1
+    return f
+
+
+@pytest.mark.parametrize("kinds", [[0], [2], [0, 0], [0, 2], [2, 2], [0, 0, 0], [2, 0, 2, 0], [1], [3], [1, 3]])
+def test_flop_model_counts(lib, kinds):
+    from paper_2301_06399_gb300 import mpt
+
+    f_iter, f_eval, sfu = mpt.flop_model(kinds)
+    assert f_iter == _chol_solve_flops(2 * len(kinds))
+    assert f_eval > 50 * len(kinds)
+    # one reciprocal square root per segment, one more per paraboloid normal,
+    # two sin/cos pairs per arc (point and tangent; 2 SFU operations each)
+    n = len(kinds)
+    assert sfu == (n + 1) + kinds.count(1) + 4 * kinds.count(3)
+
+
+def test_flop_model_rejects_bad_arguments(lib):
+    from paper_2301_06399_gb300 import mpt
+
+    with pytest.raises(RuntimeError):
+        mpt.flop_model([0, 0, 0, 0, 0])
+    with pytest.raises(RuntimeError):
+        mpt.flop_model([7])
+
+
+def test_null_arguments_are_rejected_without_a_gpu(lib):
+    # argument checks run on the host before any CUDA call
+    assert lib.mpt_scene_upload(None, None, None) == 1
+    assert lib.mpt_solve(None, None, None, None, 0, None, None, None) == 1
+    assert lib.mpt_validate(None, None, None, None, None, C.c_double(1e-20), None, None, None) == 1
+    assert lib.mpt_grad(None, None, None, None, None, None, None, None, None, None, None, None) == 1
+    assert lib.mpt_enumerate(None, None, None, 2, None, None, None, None) == 1
+    assert lib.mpt_ctx_destroy(None) == 1
