@@ -239,7 +239,9 @@ def run_ours(args):
         stream.synchronize()
         n_valid = paths.n()
         flops = algorithmic_flops(mpt, sc, cands, sols, n_cand)
-        launches_per_step = 2 + 4 + 3 + 1  # enumerate, solve (orders 1-4), validate, grad
+        # enumerate (2) + solve (endpoint copy, 4 orders x {solver, visibility
+        # prescreen, refinement}) + validate (3) + adjoint (1)
+        launches_per_step = 2 + (1 + 4 * 3) + 3 + 1
 
         # ---- device-resident timing
         ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -350,7 +352,7 @@ def run_ours(args):
                    "parallelism": f"weak: one process per GPU, {ws} GPU(s)"},
         "valid_paths_per_step": n_valid,
         "valid_paths_per_sec": n_valid * ws / (ms_per_step * 1e-3),
-        "roofline": {"kernel": "mpt_solve (k_solve, orders 1-4)", "bound": "alu",
+        "roofline": {"kernel": "mpt_solve (k_gn orders 1-4 + visibility prescreen + k_refine)", "bound": "alu",
                      "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {SM_MAX_MHZ_NOMINAL:.0f} MHz (derived)",
                      "solve_ms": solve_avg_ms, "fp32_flops_per_launch": flops,

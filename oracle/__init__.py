@@ -140,7 +140,7 @@ class Solutions:
 
 def solve(scene, table: SequenceTable, begin: int = 0, end: int | None = None, init_seed: int = 0,
           threads: int = 0) -> Solutions:
-    """Levenberg-Marquardt solve of candidates [begin, end) (c = entry * n_pairs + pair)."""
+    """Gauss-Newton solve of candidates [begin, end) (c = entry * n_pairs + pair)."""
     L = lib()
     ref = SceneRef(scene)
     n_pairs = scene.n_pairs

@@ -4,7 +4,7 @@
 // load this library.  The CUDA library never links it and shares no code,
 // headers or tables with it.  Everything here is deliberately plain: FP64
 // throughout, forward-mode dual numbers for every derivative (the CUDA path
-// uses hand-derived Jacobians), Levenberg-Marquardt with a dense Gaussian
+// uses hand-derived Jacobians), Gauss-Newton with a dense Gaussian
 // elimination, brute-force visibility against every occluder.
 //
 // What each part follows in the paper (arXiv 2301.06399):
@@ -17,7 +17,8 @@
 //                  with the normal of Eq. 2; Eq. 9 as printed with the edge
 //                  tangent of Eq. 4
 //   minimiser      find_minimum_path of Algorithm 1 (the paper leaves the
-//                  solver open; Levenberg-Marquardt is used here)
+//                  solver open; it is read as Gauss-Newton with a
+//                  backtracking line search and fixed stopping rules)
 //   candidates     all_simple_paths of Algorithm 1 (ordered sequences of
 //                  distinct objects, up to n_t interactions), optional
 //                  adjacency mask (Sec. III, Fig. 5)
@@ -373,74 +374,91 @@ struct SolveOut {
   int iters;
 };
 
-// Levenberg-Marquardt on C = ||I(X(T))||^2 (Eq. 15): lambda0 = 1e-3, x10 on
-// rejection, /10 on acceptance, Marquardt diagonal scaling, <= 200 outer
-// iterations; stop when C < 1e-30 or an accepted step is below 1e-14 S in
-// every parameter; divergence when a point leaves the cube of half-side 1e3 S.
-SolveOut lm_solve(const OracleScene& s, int n, const int32_t* ids, const double* a, const double* b,
+// Gauss-Newton step from the normal equations at x: (J^T J + mu diag) dx = -J^T rho,
+// mu = 1e-12 relative damping.  Returns the predicted decrease -g.dx.
+bool gn_step(int q, int m, const double* J, const double* rho, double* dx, double* pred) {
+  double A[MAXQ * MAXQ], g[MAXQ];
+  for (int i = 0; i < q; ++i) {
+    g[i] = 0;
+    for (int r = 0; r < m; ++r) g[i] += J[r * q + i] * rho[r];
+    for (int j = 0; j < q; ++j) {
+      double acc = 0;
+      for (int r = 0; r < m; ++r) acc += J[r * q + i] * J[r * q + j];
+      A[i * q + j] = acc;
+    }
+  }
+  for (int i = 0; i < q; ++i) {
+    A[i * q + i] += 1e-12 * A[i * q + i] + 1e-300;
+    dx[i] = -g[i];
+  }
+  if (!dense_solve(q, A, dx)) return false;
+  double p = 0;
+  for (int i = 0; i < q; ++i) p -= g[i] * dx[i];
+  *pred = p;
+  return true;
+}
+
+// find_minimum_path (Algorithm 1) read as Gauss-Newton with a backtracking
+// line search on C = ||I(X(T))||^2 (Eq. 15):
+//   - each trial point T + alpha dx costs one evaluation; a trial is accepted
+//     when it lowers C, then a new step is solved with alpha = 1, otherwise
+//     alpha is halved; alpha < 1/16 ends the search (stalled);
+//   - converged when C < 1e-30 or an accepted step moved every parameter by
+//     less than 1e-14 S; at most 24 accepted steps and 40 evaluations;
+//   - diverged when a parameter exceeds 1e3 S;
+//   - a local minimum with non-zero residual ends the search: after two
+//     accepted steps, C > 1e-3 while the Gauss-Newton model predicts a
+//     decrease below 1e-4 C.
+SolveOut gn_solve(const OracleScene& s, int n, const int32_t* ids, const double* a, const double* b,
                   const double* T0) {
   SolveOut o;
   const int q = n_params(s, n, ids);
-  double x[MAXQ], rho[MAXM], J[MAXM * MAXQ];
+  double x[MAXQ], rho[MAXM], J[MAXM * MAXQ], dx[MAXQ];
   std::memcpy(x, T0, sizeof(double) * q);
   int m = residual_jacobian(s, n, ids, a, b, x, rho, J);
   double C = 0;
   for (int i = 0; i < m; ++i) C += rho[i] * rho[i];
-  double lam = 1e-3;
-  o.status = ST_MAXITER;
+  int evals = 1;
   o.iters = 0;
-  if (!std::isfinite(C)) o.status = ST_NONFINITE;
-  for (int it = 0; it < 200 && o.status == ST_MAXITER; ++it) {
-    o.iters = it + 1;
-    if (C < 1e-30) { o.status = ST_CONVERGED; break; }
-    double A[MAXQ * MAXQ], g[MAXQ];
-    for (int i = 0; i < q; ++i) {
-      g[i] = 0;
-      for (int r = 0; r < m; ++r) g[i] += J[r * q + i] * rho[r];
-      for (int j = 0; j < q; ++j) {
-        double acc = 0;
-        for (int r = 0; r < m; ++r) acc += J[r * q + i] * J[r * q + j];
-        A[i * q + j] = acc;
-      }
-    }
-    bool accepted = false;
-    double step_inf = 0;
-    while (!accepted) {
-      double M[MAXQ * MAXQ], dx[MAXQ];
-      std::memcpy(M, A, sizeof(double) * q * q);
+  o.status = ST_MAXITER;
+  double pred = 0;
+  if (!std::isfinite(C)) {
+    o.status = ST_NONFINITE;
+  } else if (C < 1e-30) {
+    o.status = ST_CONVERGED;
+  } else if (!gn_step(q, m, J, rho, dx, &pred)) {
+    o.status = ST_STALLED;
+  } else {
+    double alpha = 1.0;
+    for (;;) {
+      double xt[MAXQ];
+      double smax = 0;
       for (int i = 0; i < q; ++i) {
-        M[i * q + i] += lam * (A[i * q + i] + 1e-300);
-        dx[i] = -g[i];
+        xt[i] = x[i] + alpha * dx[i];
+        smax = std::max(smax, std::fabs(alpha * dx[i]));
       }
-      if (dense_solve(q, M, dx)) {
-        double xn[MAXQ];
-        for (int i = 0; i < q; ++i) xn[i] = x[i] + dx[i];
-        double Cn = cost_at(s, n, ids, a, b, xn);
-        if (std::isfinite(Cn) && Cn < C) {
-          accepted = true;
-          step_inf = 0;
-          for (int i = 0; i < q; ++i) step_inf = std::max(step_inf, std::fabs(dx[i]));
-          std::memcpy(x, xn, sizeof(double) * q);
-          lam = std::max(lam * 0.1, 1e-15);
-          break;
-        }
+      const double Ct = cost_at(s, n, ids, a, b, xt);
+      ++evals;
+      if (std::isfinite(Ct) && Ct < C) {
+        std::memcpy(x, xt, sizeof(double) * q);
+        C = Ct;
+        ++o.iters;
+        double pmax = 0;
+        for (int i = 0; i < q; ++i) pmax = std::max(pmax, std::fabs(x[i]));
+        if (!(pmax <= 1e3 * s.scale)) { o.status = ST_DIVERGED; break; }
+        if (C < 1e-30 || smax < 1e-14 * s.scale) { o.status = ST_CONVERGED; break; }
+        if (o.iters >= 24) { o.status = ST_MAXITER; break; }
+        if (evals >= 40) { o.status = ST_MAXITER; break; }
+        m = residual_jacobian(s, n, ids, a, b, x, rho, J);
+        if (!gn_step(q, m, J, rho, dx, &pred)) { o.status = ST_STALLED; break; }
+        alpha = 1.0;
+        if (o.iters >= 2 && C > 1e-3 && pred < 1e-4 * C) { o.status = ST_STALLED; break; }
+      } else {
+        alpha *= 0.5;
+        if (alpha < 1.0 / 16.0) { o.status = ST_STALLED; break; }
+        if (evals >= 40) { o.status = ST_MAXITER; break; }
       }
-      lam *= 10.0;
-      if (lam > 1e20) break;
     }
-    if (!accepted) { o.status = ST_STALLED; break; }
-    m = residual_jacobian(s, n, ids, a, b, x, rho, J);
-    C = 0;
-    for (int i = 0; i < m; ++i) C += rho[i] * rho[i];
-    double r[MAXM];
-    V3d X[MAXN];
-    path_residual<double>(s, n, ids, ld(a), ld(b), x, nullptr, r, X);
-    double xmax = 0;
-    for (int k = 0; k < n; ++k)
-      xmax = std::max({xmax, std::fabs(X[k].x), std::fabs(X[k].y), std::fabs(X[k].z)});
-    if (!(xmax <= 1e3 * s.scale)) { o.status = ST_DIVERGED; break; }
-    if (!std::isfinite(C)) { o.status = ST_NONFINITE; break; }
-    if (C < 1e-30 || step_inf < 1e-14 * s.scale) { o.status = ST_CONVERGED; break; }
   }
   std::memcpy(o.T, x, sizeof(double) * q);
   o.cost = C;
@@ -709,7 +727,7 @@ int oracle_solve(const OracleScene* sc, int64_t n_entries, const int32_t* ent_or
       initial_params(s, ids[k], Y, init_seed, p, packed, ent_start[e], k, T0 + off);
       off += dof(s.obj_kind[ids[k]]);
     }
-    SolveOut o = lm_solve(s, n, ids, a, b, T0);
+    SolveOut o = gn_solve(s, n, ids, a, b, T0);
     double r[MAXM];
     V3d X[MAXN];
     path_residual<double>(s, n, ids, A, B, o.T, nullptr, r, X);

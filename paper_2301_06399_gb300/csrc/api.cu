@@ -7,10 +7,6 @@
 
 #include "mpt_internal.cuh"
 
-// The FLOP model instantiates the __host__ __device__ kernel math with a
-// host-only counting scalar; that instantiation never runs on the device.
-#pragma nv_diag_suppress 20014
-
 namespace mpt {
 
 int64_t host_candidate_count(const mpt_scene* scene, const mpt_endpoints* ends, int max_order,
@@ -80,58 +76,6 @@ static bool convert_occluder(int kind, const double* p, double* v) {
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
-// ------------------------------------------------------ FLOP counting --
-// Scalar that counts its FP32-pipe operations (add/sub/mul = 1, fma = 2)
-// and its special-function operations separately.
-struct Cnt {
-  float v;
-  Cnt() : v(0) {}
-  Cnt(float x) : v(x) {}   // NOLINT
-  Cnt(double x) : v((float)x) {}  // NOLINT
-  Cnt(int x) : v((float)x) {}  // NOLINT
-};
-static thread_local double g_flops = 0, g_sfu = 0;
-inline Cnt operator+(Cnt a, Cnt b) { g_flops += 1; return Cnt(a.v + b.v); }
-inline Cnt operator-(Cnt a, Cnt b) { g_flops += 1; return Cnt(a.v - b.v); }
-inline Cnt operator*(Cnt a, Cnt b) { g_flops += 1; return Cnt(a.v * b.v); }
-inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
-inline bool operator<(Cnt a, Cnt b) { return a.v < b.v; }
-inline bool operator>(Cnt a, Cnt b) { return a.v > b.v; }
-inline bool operator<=(Cnt a, Cnt b) { return a.v <= b.v; }
-inline bool operator>=(Cnt a, Cnt b) { return a.v >= b.v; }
-inline Cnt fma_(Cnt a, Cnt b, Cnt c) { g_flops += 2; return Cnt(a.v * b.v + c.v); }
-inline Cnt rsq(Cnt a) { g_sfu += 1; return Cnt(1.0f / std::sqrt(a.v)); }
-inline void sincos_(Cnt x, Cnt& s, Cnt& c) { g_sfu += 2; s = Cnt(std::sin(x.v)); c = Cnt(std::cos(x.v)); }
-
-template <int N>
-static void count_model(const int32_t* kinds, double* f_eval, double* f_iter, double* sfu_eval) {
-  int kind[N];
-  Rec<Cnt> rec[N];
-  Cnt prm[2 * N];
-  for (int k = 0; k < N; ++k) {
-    kind[k] = kinds[k];
-    for (int i = 0; i < 16; ++i) rec[k].v[i] = Cnt(0.1f * (i + 1) + k);
-    rec[k].v[3] = Cnt(2.0f);
-    prm[2 * k] = Cnt(0.3f + k);
-    prm[2 * k + 1] = Cnt(0.7f - k);
-  }
-  v3<Cnt> A = mk(Cnt(-5.0f), Cnt(1.0f), Cnt(3.0f)), B = mk(Cnt(6.0f), Cnt(-2.0f), Cnt(4.0f));
-  constexpr int Q = 2 * N;
-  Cnt jtj[Q * (Q + 1) / 2], g[Q], x[Q];
-  bool ok;
-  g_flops = 0;
-  g_sfu = 0;
-  eval_path<N, Cnt, Cnt, true>(kind, rec, prm, A, B, jtj, g, ok);
-  // trial point update alpha * dlt + prm
-  *f_eval = g_flops + 2.0 * Q;
-  *sfu_eval = g_sfu;
-  for (int i = 0; i < Q * (Q + 1) / 2; ++i) jtj[i] = Cnt(i == 0 ? 4.0f : 0.5f);
-  g_flops = 0;
-  cholesky<Q, Cnt>(jtj, Cnt(1e-6f));
-  chol_solve<Q, Cnt>(jtj, g, x);
-  *f_iter = g_flops;
-}
 
 }  // namespace mpt
 
@@ -347,24 +291,6 @@ int mpt_grad(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, co
   if (check_ends(ends) != MPT_OK) return MPT_ERR_ARG;
   return launch_grad(ctx, scene, ends, cand, paths, d_valid_count, g_len, g_pts, g_tx, g_rx, g_obj,
                      reinterpret_cast<cudaStream_t>(stream));
-}
-
-int mpt_flop_model(int order, const int32_t* kinds, double* flops_per_iter, double* flops_per_eval,
-                   double* sfu_per_eval) {
-  if (order < 1 || order > 4 || !kinds || !flops_per_iter || !flops_per_eval) return MPT_ERR_ARG;
-  for (int k = 0; k < order; ++k)
-    if (kinds[k] < 0 || kinds[k] > 3) return MPT_ERR_ARG;
-  double fe = 0, fi = 0, sfu = 0;
-  switch (order) {
-    case 1: count_model<1>(kinds, &fe, &fi, &sfu); break;
-    case 2: count_model<2>(kinds, &fe, &fi, &sfu); break;
-    case 3: count_model<3>(kinds, &fe, &fi, &sfu); break;
-    default: count_model<4>(kinds, &fe, &fi, &sfu); break;
-  }
-  *flops_per_iter = fi;
-  *flops_per_eval = fe;
-  if (sfu_per_eval) *sfu_per_eval = sfu;
-  return MPT_OK;
 }
 
 }  // extern "C"

@@ -35,8 +35,10 @@ MPT_HD float rsq(float x) {
   return 1.0f / sqrtf(x);
 #endif
 }
+MPT_HD float d2f_bits(double x);
+MPT_HD double f2d_bits(float f);
 MPT_HD double rsq(double x) {
-  double y = (double)rsq((float)x);
+  double y = f2d_bits(rsq(d2f_bits(x)));
   double h = 0.5 * x;
   y = y * fma(-h * y, y, 1.5);
   y = y * fma(-h * y, y, 1.5);
@@ -78,7 +80,51 @@ template <class T> MPT_HD v3<T> axpy(T s, const v3<T>& b, const v3<T>& a) {
 template <class T> MPT_HD v3<T> cross(const v3<T>& a, const v3<T>& b) {
   return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
-template <class D, class S> MPT_HD v3<D> cvt(const v3<S>& a) { return mk(D(a.x), D(a.y), D(a.z)); }
+// double -> float on the integer units (truncating the mantissa; |error| <
+// 1 ulp).  The mixed-precision evaluation converts every Jacobian input;
+// GB300's FP64 pipe (which executes hardware conversions) is 1/64 of FP32.
+MPT_HD float d2f_bits(double x) {
+#if defined(__CUDA_ARCH__)
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(u >> 63) << 31;
+  const unsigned ex = (unsigned)((u >> 52) & 0x7FFu);
+  const unsigned m = (unsigned)((u >> 29) & 0x7FFFFFu);
+  if (ex == 0x7FFu) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+  const int e = (int)ex - 1023 + 127;
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  if (e <= 0) return __uint_as_float(sign);
+  return __uint_as_float(sign | ((unsigned)e << 23) | m);
+#else
+  return (float)x;
+#endif
+}
+// Exact float -> double, also on the integer units.  FP32 subnormals (never
+// produced by the solver's magnitudes) become +-0.
+MPT_HD double f2d_bits(float f) {
+#if defined(__CUDA_ARCH__)
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t s = (uint64_t)(u >> 31) << 63;
+  const uint32_t e = (u >> 23) & 0xFFu;
+  const uint64_t m = (uint64_t)(u & 0x7FFFFFu) << 29;
+  uint64_t d;
+  if (e == 0) d = s;
+  else if (e == 0xFFu) d = s | (0x7FFull << 52) | m;
+  else d = s | ((uint64_t)(e + 896u) << 52) | m;
+  return __longlong_as_double((long long)d);
+#else
+  return (double)f;
+#endif
+}
+template <class D, class S>
+struct Conv {
+  MPT_HD static D go(S x) { return D(x); }
+};
+template <>
+struct Conv<float, double> {
+  MPT_HD static float go(double x) { return d2f_bits(x); }
+};
+template <class D, class S> MPT_HD D conv(S x) { return Conv<D, S>::go(x); }
+template <class D, class S> MPT_HD v3<D> cvt(const v3<S>& a) { return mk(conv<D>(a.x), conv<D>(a.y), conv<D>(a.z)); }
 
 // ------------------------------------------------------------ scene record --
 // 16 values per object (same layout in FP32 and FP64 copies):
@@ -106,7 +152,9 @@ struct PointT {
   v3<T> X, w0, w1;
 };
 
-template <class T, bool TANGENTS>
+// CURVED = false instantiates the planes-and-straight-edges solver only (no
+// paraboloid or arc branches: less code, fewer registers).
+template <class T, bool TANGENTS, bool CURVED = true>
 MPT_HD PointT<T> point_at(int kind, const Rec<T>& r, T s, T t) {
   PointT<T> p;
   const T zero = T(0);
@@ -114,7 +162,7 @@ MPT_HD PointT<T> point_at(int kind, const Rec<T>& r, T s, T t) {
   if (kind == K_PLANE) {
     p.X = axpy(t, r.f3(8), axpy(s, r.f3(4), r.f3(0)));
     if (TANGENTS) { p.w0 = r.f3(4); p.w1 = r.f3(8); }
-  } else if (kind == K_PARAB) {
+  } else if (CURVED && kind == K_PARAB) {
     const T q4 = r.v[12], q2 = r.v[14];
     T h = (s * s + t * t) * q4;
     v3<T> base = mk(r.v[3], r.v[7], r.v[11]);
@@ -123,7 +171,7 @@ MPT_HD PointT<T> point_at(int kind, const Rec<T>& r, T s, T t) {
       p.w0 = axpy(s * q2, r.f3(8), r.f3(0));
       p.w1 = axpy(t * q2, r.f3(8), r.f3(4));
     }
-  } else if (kind == K_LINE) {
+  } else if (!CURVED || kind == K_LINE) {
     p.X = axpy(s, r.f3(4), r.f3(0));
     if (TANGENTS) p.w0 = r.f3(4);
   } else {
@@ -146,7 +194,7 @@ struct NormalEq {
   static constexpr int P = Q * (Q + 1) / 2;
 };
 
-// Adds one column block's contribution: for the (up to) six parameter
+// Adds one interaction's contribution: for the (up to) six parameter
 // columns of interaction k (previous point, this point, next point), the
 // column vectors col[c] (3 rows for reflection, 1 for diffraction) give
 // J^T J entries <col[a], col[b]> and J^T rho entries <col[a], rho>.
@@ -177,12 +225,25 @@ MPT_HD void accumulate(int k, const J (&col)[6][ROWS], const bool (&live)[6], co
 // interaction k; edges use slot 2k) and, when WANT_J, accumulates the normal
 // equations J^T J (packed, Q = 2N) and g = J^T rho.  A = TX, B = RX.
 // Returns the cost; `ok` is false when a segment has zero length.
-template <int N, class R, class J, bool WANT_J>
+//
+// Hand-derived Jacobian.  With unit segment directions u_j and inverse
+// lengths l_j, a tangent w of point k enters through the projections
+//   Pi_k(w) = (w - u_k <u_k, w>) l_k        (incoming segment of point k)
+//   Pr_k(w) = (w - u_{k+1} <u_{k+1}, w>) l_{k+1}   (outgoing segment)
+// Reflection rho_k = r - i + 2<i,n>n, H(v) = v - 2<n,v>n:
+//   d rho_k / d(point k-1) = H(Pi_k w) = H(Pr_{k-1} w)
+//   d rho_k / d(point k)   = -(Pr_k w + H(Pi_k w))  (+ normal variation)
+//   d rho_k / d(point k+1) = Pr_k w = Pi_{k+1} w
+// Diffraction rho_k = <i,e> - <r,e>:
+//   -<e, Pr_{k-1} w>,  <e, Pi_k w> + <e, Pr_k w> (+ edge variation),  -<e, Pi_{k+1} w>
+// so each projection is computed once per point and shared by neighbours.
+template <int N, class R, class J, bool WANT_J, bool CURVED = true>
 MPT_HD R eval_path(const int (&kind)[N], const Rec<R> (&rec)[N], const R (&prm)[2 * N], const v3<R>& A,
                    const v3<R>& B, J* jtj, J* g, bool& ok) {
   PointT<R> pt[N];
 #pragma unroll
-  for (int k = 0; k < N; ++k) pt[k] = point_at<R, WANT_J>(kind[k], rec[k], prm[2 * k], prm[2 * k + 1]);
+  for (int k = 0; k < N; ++k)
+    pt[k] = point_at<R, WANT_J, CURVED>(kind[k], rec[k], prm[2 * k], prm[2 * k + 1]);
   // segment unit vectors u[j] = (X_{j+1} - X_j)/||.||, inverse lengths il[j]
   v3<R> u[N + 1];
   R il[N + 1];
@@ -197,29 +258,54 @@ MPT_HD R eval_path(const int (&kind)[N], const Rec<R> (&rec)[N], const R (&prm)[
     il[j] = rsq(l2);
     u[j] = d * il[j];
   }
+  v3<J> PiW[N][2], PrW[N][2];
   if (WANT_J) {
 #pragma unroll
     for (int i = 0; i < NormalEq<N>::P; ++i) jtj[i] = J(0);
 #pragma unroll
     for (int i = 0; i < 2 * N; ++i) g[i] = J(0);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const v3<J> ui = cvt<J>(u[k]), uo = cvt<J>(u[k + 1]);
+      const J li = conv<J>(il[k]), lo = conv<J>(il[k + 1]);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const v3<J> w = cvt<J>(j == 0 ? pt[k].w0 : pt[k].w1);
+        if (j == 1 && is_edge(kind[k])) {
+          PiW[k][j] = w;  // zero tangent
+          PrW[k][j] = w;
+        } else {
+          PiW[k][j] = axpy(-dot(ui, w), ui, w) * li;
+          PrW[k][j] = axpy(-dot(uo, w), uo, w) * lo;
+        }
+      }
+    }
   }
   R cost = R(0);
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const v3<R>& ih = u[k];      // incident direction (into X_k)
     const v3<R>& rh = u[k + 1];  // departing direction
+    // columns of the neighbours: live unless the neighbour is an edge's unused slot
+    bool live[6];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      live[j] = (k >= 1) && (j == 0 || !is_edge(kind[k > 0 ? k - 1 : 0]));
+      live[2 + j] = (j == 0) || !is_edge(kind[k]);
+      live[4 + j] = (k + 1 < N) && (j == 0 || !is_edge(kind[k + 1 < N ? k + 1 : k]));
+    }
     if (!is_edge(kind[k])) {
       // ---- reflection: rho = r_hat - i_hat + 2 <i_hat, n> n  (Eq. 8 / ||i||)
       v3<R> nh;
       R inv_nn = R(0);
-      v3<R> nraw;
-      if (kind[k] == K_PLANE) {
+      if (!CURVED || kind[k] == K_PLANE) {
         nh = rec[k].f3(12);
       } else {
         // n = c2 - (s/(2f)) c0 - (t/(2f)) c1  (gradient of the implicit
         // paraboloid, Eq. 2, up to sign and scale)
         const R q2 = rec[k].v[14];
-        nraw = axpy(-prm[2 * k + 1] * q2, rec[k].f3(4), axpy(-prm[2 * k] * q2, rec[k].f3(0), rec[k].f3(8)));
+        const v3<R> nraw =
+            axpy(-prm[2 * k + 1] * q2, rec[k].f3(4), axpy(-prm[2 * k] * q2, rec[k].f3(0), rec[k].f3(8)));
         inv_nn = rsq(dot(nraw, nraw));
         nh = nraw * inv_nn;
       }
@@ -227,59 +313,35 @@ MPT_HD R eval_path(const int (&kind)[N], const Rec<R> (&rec)[N], const R (&prm)[
       v3<R> rho = axpy(R(2) * c, nh, rh - ih);
       cost = fma_(rho.x, rho.x, fma_(rho.y, rho.y, fma_(rho.z, rho.z, cost)));
       if (WANT_J) {
-        const v3<J> iJ = cvt<J>(ih), rJ = cvt<J>(rh), nJ = cvt<J>(nh);
-        const J ia = J(il[k]), ib = J(il[k + 1]);
-        J col[6][3];
-        bool live[6];
-        // P_i w / ||i|| and P_r w / ||r||
-        auto Pi = [&](const v3<J>& w) { return axpy(-dot(iJ, w), iJ, w) * ia; };
-        auto Pr = [&](const v3<J>& w) { return axpy(-dot(rJ, w), rJ, w) * ib; };
+        const v3<J> iJ = cvt<J>(ih), nJ = cvt<J>(nh);
         auto H = [&](const v3<J>& w) { return axpy(J(-2) * dot(nJ, w), nJ, w); };
+        J col[6][3];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          // previous point (k-1): H P_i w / ||i||
-          live[j] = (k >= 1) && (j == 0 || !is_edge(kind[k > 0 ? k - 1 : 0]));
-          if (k >= 1) {
-            const v3<J> w = cvt<J>(j == 0 ? pt[k - 1].w0 : pt[k - 1].w1);
-            v3<J> v = H(Pi(w));
-            col[j][0] = v.x; col[j][1] = v.y; col[j][2] = v.z;
-          } else {
-            col[j][0] = col[j][1] = col[j][2] = J(0);
+          const v3<J> vp = (k >= 1) ? H(PrW[k > 0 ? k - 1 : 0][j]) : mk(J(0), J(0), J(0));
+          col[j][0] = vp.x; col[j][1] = vp.y; col[j][2] = vp.z;
+          v3<J> vs = -(PrW[k][j] + H(PiW[k][j]));
+          if (CURVED && kind[k] == K_PARAB) {
+            // d/dT of 2 <i,n> n through n: 2 (<i, dn> n + <i, n> dn),
+            // dn = (I - n n^T) dn_raw / ||n_raw||, dn_raw = -c_j / (2f)
+            const J q2 = conv<J>(rec[k].v[14]);
+            const v3<J> craw = cvt<J>(j == 0 ? rec[k].f3(0) : rec[k].f3(4)) * (-q2);
+            const v3<J> dn = axpy(-dot(nJ, craw), nJ, craw) * conv<J>(inv_nn);
+            vs = axpy(J(2) * dot(iJ, dn), nJ, vs);
+            vs = axpy(J(2) * conv<J>(c), dn, vs);
           }
-          // this point: -P_r w/||r|| - H P_i w/||i|| (+ normal variation)
-          live[2 + j] = true;
-          {
-            const v3<J> w = cvt<J>(j == 0 ? pt[k].w0 : pt[k].w1);
-            v3<J> v = -(Pr(w) + H(Pi(w)));
-            if (kind[k] == K_PARAB) {
-              // d/dT of 2 <i,n> n through n: 2 (<i, dn> n + <i, n> dn),
-              // dn = (I - n n^T) dn_raw / ||n_raw||, dn_raw = -c_j / (2f)
-              const J q2 = J(rec[k].v[14]);
-              const v3<J> craw = cvt<J>(j == 0 ? rec[k].f3(0) : rec[k].f3(4)) * (-q2);
-              const v3<J> dn = axpy(-dot(nJ, craw), nJ, craw) * J(inv_nn);
-              v = axpy(J(2) * dot(iJ, dn), nJ, v);
-              v = axpy(J(2) * J(c), dn, v);
-            }
-            col[2 + j][0] = v.x; col[2 + j][1] = v.y; col[2 + j][2] = v.z;
-          }
-          // next point (k+1): P_r w / ||r||
-          live[4 + j] = (k + 1 < N) && (j == 0 || !is_edge(kind[k + 1 < N ? k + 1 : k]));
-          if (k + 1 < N) {
-            const v3<J> w = cvt<J>(j == 0 ? pt[k + 1].w0 : pt[k + 1].w1);
-            v3<J> v = Pr(w);
-            col[4 + j][0] = v.x; col[4 + j][1] = v.y; col[4 + j][2] = v.z;
-          } else {
-            col[4 + j][0] = col[4 + j][1] = col[4 + j][2] = J(0);
-          }
+          col[2 + j][0] = vs.x; col[2 + j][1] = vs.y; col[2 + j][2] = vs.z;
+          const v3<J> vn = (k + 1 < N) ? PiW[k + 1 < N ? k + 1 : k][j] : mk(J(0), J(0), J(0));
+          col[4 + j][0] = vn.x; col[4 + j][1] = vn.y; col[4 + j][2] = vn.z;
         }
-        const J rr[3] = {J(rho.x), J(rho.y), J(rho.z)};
+        const J rr[3] = {conv<J>(rho.x), conv<J>(rho.y), conv<J>(rho.z)};
         accumulate<N, 3, J>(k, col, live, rr, jtj, g);
       }
     } else {
       // ---- diffraction: rho = <i_hat, e> - <r_hat, e>  (Eq. 9)
       v3<R> eh;
       v3<R> de;  // d e / d phi for arcs
-      if (kind[k] == K_LINE) {
+      if (!CURVED || kind[k] == K_LINE) {
         eh = rec[k].f3(4);
       } else {
         R sn, cs;
@@ -290,33 +352,18 @@ MPT_HD R eval_path(const int (&kind)[N], const Rec<R> (&rec)[N], const R (&prm)[
       const R rho = dot(ih, eh) - dot(rh, eh);
       cost = fma_(rho, rho, cost);
       if (WANT_J) {
-        const v3<J> iJ = cvt<J>(ih), rJ = cvt<J>(rh), eJ = cvt<J>(eh);
-        const J ia = J(il[k]), ib = J(il[k + 1]);
-        const J ei = dot(eJ, iJ), er = dot(eJ, rJ);
-        // <e, P_i w>/||i|| = (<e,w> - <e,i><i,w>)/||i||, same for r
-        auto ePi = [&](const v3<J>& w) { return (dot(eJ, w) - ei * dot(iJ, w)) * ia; };
-        auto ePr = [&](const v3<J>& w) { return (dot(eJ, w) - er * dot(rJ, w)) * ib; };
+        const v3<J> eJ = cvt<J>(eh);
         J col[6][1];
-        bool live[6];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          live[j] = (k >= 1) && (j == 0 || !is_edge(kind[k > 0 ? k - 1 : 0]));
-          col[j][0] = (k >= 1) ? -ePi(cvt<J>(j == 0 ? pt[k > 0 ? k - 1 : 0].w0 : pt[k > 0 ? k - 1 : 0].w1)) : J(0);
-          live[4 + j] = (k + 1 < N) && (j == 0 || !is_edge(kind[k + 1 < N ? k + 1 : k]));
-          col[4 + j][0] = (k + 1 < N) ? -ePr(cvt<J>(j == 0 ? pt[k + 1 < N ? k + 1 : k].w0
-                                                            : pt[k + 1 < N ? k + 1 : k].w1))
-                                      : J(0);
+          col[j][0] = (k >= 1) ? -dot(eJ, PrW[k > 0 ? k - 1 : 0][j]) : J(0);
+          col[4 + j][0] = (k + 1 < N) ? -dot(eJ, PiW[k + 1 < N ? k + 1 : k][j]) : J(0);
         }
-        {
-          const v3<J> w = cvt<J>(pt[k].w0);
-          J v = ePi(w) + ePr(w);
-          if (kind[k] == K_ARC) v = v + dot(iJ - rJ, cvt<J>(de));  // edge direction variation
-          col[2][0] = v;
-          live[2] = true;
-          col[3][0] = J(0);
-          live[3] = false;
-        }
-        const J rr[1] = {J(rho)};
+        J v = dot(eJ, PiW[k][0]) + dot(eJ, PrW[k][0]);
+        if (CURVED && kind[k] == K_ARC) v = v + dot(cvt<J>(ih - rh), cvt<J>(de));  // edge direction variation
+        col[2][0] = v;
+        col[3][0] = J(0);
+        const J rr[1] = {conv<J>(rho)};
         accumulate<N, 1, J>(k, col, live, rr, jtj, g);
       }
     }

@@ -68,21 +68,6 @@ struct RefineList {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int CHUNK = 256;  // candidates a warp claims at once (8 per lane)
 
-// Exact float -> double by assembling the bits on the integer units (the
-// FP64 pipe of GB300 is 1/64 of FP32, so conversions there are costly).
-// FP32 subnormals (never produced by the solver's magnitudes) become +-0.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint64_t s = (uint64_t)(u >> 31) << 63;
-  const uint32_t e = (u >> 23) & 0xFFu;
-  const uint64_t m = (uint64_t)(u & 0x7FFFFFu) << 29;
-  uint64_t d;
-  if (e == 0) d = s;
-  else if (e == 0xFFu) d = s | (0x7FFull << 52) | m;
-  else d = s | ((uint64_t)(e + 896u) << 52) | m;
-  return __longlong_as_double((long long)d);
-}
-
 // FP32 copies of the endpoints, made once per solve call.
 __global__ void k_ends_f32(const double* tx, int n_tx, const double* rx, int n_rx, float4* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -196,7 +181,14 @@ __device__ __forceinline__ uint64_t pack_ids(const Cand& cd, int n) {
 // With a counter, the warp claims CHUNK-sized pieces of the range as it goes
 // (work stealing between warps); without one it takes [begin, end) as its
 // single chunk.  order_base = first candidate of order N (refine-list base).
-template <int N, int PREC>
+//
+// A lane that finishes keeps its result and goes idle; idle lanes write their
+// results and take new candidates together, once REFILL_MIN of them are idle
+// (or nothing else is running), so the narrow write/refill code runs for many
+// lanes at once instead of once per finishing lane.
+constexpr int REFILL_MIN = 8;
+
+template <int N, int PREC, bool CURVED>
 __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, const float4* ends32,
                                         const CandView& cv, const SolView& out, const SolveCfg& cfg,
                                         unsigned long long* counter, const RefineList& rl, int64_t begin,
@@ -204,12 +196,16 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
   using R = typename std::conditional<PREC == MPT_FP64_PLAIN, double, float>::type;
   constexpr int Q = 2 * N, P = Q * (Q + 1) / 2;
   const unsigned lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
   const R c_tol = R(PREC == MPT_FP64_PLAIN ? cfg.c_tol64 : cfg.c_tol32);
   const R step_tol = R(PREC == MPT_FP64_PLAIN ? cfg.step_tol64 : cfg.step_tol32);
   const R diverge = R(cfg.diverge);
   const R mu = R(PREC == MPT_FP64_PLAIN ? cfg.mu64 : cfg.mu32);
 
-  int64_t c = -1;
+  int64_t c = -1;       // candidate being solved, -1 = idle
+  int64_t done_c = -1;  // finished candidate whose result is not written yet
+  int done_status = 0;
+  bool done_push = false;
   bool exhausted = false;
   int kind[N];
   Rec<R> rec[N];
@@ -228,33 +224,61 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
     chunk_end = end;
     range_done = true;
   }
-  const unsigned lt_mask = (1u << lane) - 1u;
   for (;;) {
-    // ---- refill idle lanes with the next candidates of the warp's chunk
-    bool need = (c < 0) && !exhausted;
-    unsigned need_mask = __ballot_sync(FULL, need);
-    while (need_mask) {
-      if (chunk_cur >= chunk_end) {
-        if (range_done) break;
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(counter, (unsigned long long)CHUNK);
-        base = __shfl_sync(FULL, base, 0);
-        chunk_cur = begin + (int64_t)base;
-        chunk_end = chunk_cur + CHUNK < end ? chunk_cur + CHUNK : end;
-        if (chunk_cur >= end) {
-          range_done = true;
-          break;
+    const unsigned idle = __ballot_sync(FULL, c < 0);
+    if (idle == FULL || __popc(idle) >= REFILL_MIN) {
+      // ---- write the results waiting in idle lanes
+      if (done_c >= 0) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) out.T[(int64_t)i * out.cap + done_c] = to_f64(prm[i]);
+        if (out.T32 != nullptr) {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) out.T32[(int64_t)i * out.cap + done_c] = (float)prm[i];
+        }
+        out.cost[done_c] = to_f64(cost);
+        out.status[done_c] = (uint8_t)done_status;
+        out.iters[done_c] = (uint8_t)min(iters, 255);
+        out.evals[done_c] = (uint8_t)min(evals, 255);
+      }
+      if (PREC == MPT_FP32_FP64REFINE) {
+        const unsigned pm = __ballot_sync(FULL, done_push);
+        if (pm) {
+          const int leader = __ffs(pm) - 1;
+          unsigned long long base = 0;
+          if ((int)lane == leader) base = atomicAdd(rl.count + (N - 1), (unsigned long long)__popc(pm));
+          base = __shfl_sync(FULL, base, leader);
+          if (done_push) {
+            const int64_t pos = (int64_t)base + __popc(pm & lt_mask);
+            rl.idx[order_base + pos] = (int32_t)(done_c - order_base);
+          }
         }
       }
-      const int avail = (int)(chunk_end - chunk_cur);
-      const int rank = __popc(need_mask & lt_mask);
-      const bool take = need && rank < avail;
-      const int64_t idx = chunk_cur + rank;
-      const int served = __popc(need_mask) < avail ? __popc(need_mask) : avail;
-      chunk_cur += served;
-      if (take) {
-        need = false;
-        {
+      done_c = -1;
+      done_push = false;
+      // ---- take the next candidates of the warp's chunk
+      bool need = (c < 0) && !exhausted;
+      unsigned need_mask = __ballot_sync(FULL, need);
+      while (need_mask) {
+        if (chunk_cur >= chunk_end) {
+          if (range_done) break;
+          unsigned long long base = 0;
+          if (lane == 0) base = atomicAdd(counter, (unsigned long long)CHUNK);
+          base = __shfl_sync(FULL, base, 0);
+          chunk_cur = begin + (int64_t)base;
+          chunk_end = chunk_cur + CHUNK < end ? chunk_cur + CHUNK : end;
+          if (chunk_cur >= end) {
+            range_done = true;
+            break;
+          }
+        }
+        const int avail = (int)(chunk_end - chunk_cur);
+        const int rank = __popc(need_mask & lt_mask);
+        const bool take = need && rank < avail;
+        const int64_t idx = chunk_cur + rank;
+        const int served = __popc(need_mask) < avail ? __popc(need_mask) : avail;
+        chunk_cur += served;
+        if (take) {
+          need = false;
           const Cand cd = decode(__ldg(cv.rec + idx));
           if (cand_in_range(sc, ep, cd) && cd.order == N) {
             c = idx;
@@ -281,21 +305,19 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
             out.evals[idx] = 0;
           }
         }
+        need_mask = __ballot_sync(FULL, need);
       }
-      need_mask = __ballot_sync(FULL, need);
+      if (range_done && c < 0) exhausted = true;
     }
-    if (range_done && c < 0) exhausted = true;
     if (__ballot_sync(FULL, c >= 0) == 0) {
-      if (__ballot_sync(FULL, !exhausted) == 0) break;
+      if (__ballot_sync(FULL, !exhausted || done_c >= 0) == 0) break;
       continue;
     }
-    bool push = false;
-    int64_t push_c = 0;
     if (c >= 0) {
       // ---- one evaluation at the trial point
       R jtj[P], g[Q];
       bool ok;
-      const R ct = eval_path<N, R, R, true>(kind, rec, trial, A, B, jtj, g, ok);
+      const R ct = eval_path<N, R, R, true, CURVED>(kind, rec, trial, A, B, jtj, g, ok);
       ++evals;
       int done = -1;
       bool factor = false;
@@ -344,59 +366,37 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
 #pragma unroll
         for (int i = 0; i < Q; ++i) trial[i] = fma_(alpha, dlt[i], prm[i]);
       } else {
-        // ---- finish: write the result, queue FP64 refinement if it may be valid
+        // ---- finish: keep the result for the next batched write
         int status = done;
         if (PREC == MPT_FP64_PLAIN) status |= MPT_PATH_REFINED;
+        bool pass = false;
         if (PREC == MPT_FP32_FP64REFINE) {
-          bool pass = isfinite(cost) && cost < R(cfg.prescreen_cost) && done != MPT_PATH_DIVERGED;
+          pass = isfinite(cost) && cost < R(cfg.prescreen_cost) && done != MPT_PATH_DIVERGED;
 #pragma unroll
           for (int k = 0; k < N; ++k)
             pass = pass && in_bounds_margin<R>(kind[k], rec[k], prm[2 * k], prm[2 * k + 1], R(cfg.prescreen_margin));
-          if (pass) {
-            push = true;
-            push_c = c;
-          } else {
-            status |= MPT_PATH_PRESCREENED;
-          }
+          if (!pass) status |= MPT_PATH_PRESCREENED;
         }
-#pragma unroll
-        for (int i = 0; i < Q; ++i) out.T[(int64_t)i * out.cap + c] = to_f64(prm[i]);
-        if (out.T32 != nullptr) {
-#pragma unroll
-          for (int i = 0; i < Q; ++i) out.T32[(int64_t)i * out.cap + c] = (float)prm[i];
-        }
-        out.cost[c] = to_f64(cost);
-        out.status[c] = (uint8_t)status;
-        out.iters[c] = (uint8_t)min(iters, 255);
-        out.evals[c] = (uint8_t)min(evals, 255);
+        done_c = c;
+        done_status = status;
+        done_push = pass;
         c = -1;
-      }
-    }
-    if (PREC == MPT_FP32_FP64REFINE) {
-      const unsigned pm = __ballot_sync(FULL, push);
-      if (pm) {
-        const int leader = __ffs(pm) - 1;
-        unsigned long long base = 0;
-        if ((int)lane == leader) base = atomicAdd(rl.count + (N - 1), (unsigned long long)__popc(pm));
-        base = __shfl_sync(FULL, base, leader);
-        if (push) {
-          const int64_t pos = (int64_t)base + __popc(pm & ((1u << lane) - 1u));
-          rl.idx[order_base + pos] = (int32_t)(push_c - order_base);
-        }
       }
     }
   }
 }
 
-template <int N, int PREC>
-__global__ void __launch_bounds__(SOLVE_BLOCK) k_gn(DevScene sc, DevEnds ep, const float4* ends32, CandView cv,
+// Orders 1-2 (the bulk of the work) are held to 128 registers: 4 blocks of
+// 128 threads per SM.
+template <int N, int PREC, bool CURVED>
+__global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? 4 : 1)) k_gn(DevScene sc, DevEnds ep, const float4* ends32, CandView cv,
                                                     SolView out, SolveCfg cfg, unsigned long long* counter,
                                                     RefineList rl) {
   int64_t end = cv.order_begin[N];
   if (end > cv.cap) end = cv.cap;
   int64_t begin = cv.order_begin[N - 1];
   if (begin > end) begin = end;
-  gn_warp<N, PREC>(sc, ep, ends32, cv, out, cfg, counter, rl, begin, end, begin);
+  gn_warp<N, PREC, CURVED>(sc, ep, ends32, cv, out, cfg, counter, rl, begin, end, begin);
 }
 
 // One launch over every order (uneven orders and convergence in one
@@ -426,10 +426,10 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_mixed(DevScene sc, DevEnds e
       if (oe <= s) oe = s + 1;
       const int64_t ob = (o >= 1 && o <= 4) ? cv.order_begin[o - 1] : 0;
       switch (o) {
-        case 1: gn_warp<1, PREC>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
-        case 2: gn_warp<2, PREC>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
-        case 3: gn_warp<3, PREC>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
-        case 4: gn_warp<4, PREC>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
+        case 1: gn_warp<1, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
+        case 2: gn_warp<2, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
+        case 3: gn_warp<3, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
+        case 4: gn_warp<4, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
         default:
           if (lane == 0) {
             out.cost[s] = (double)INFINITY;
@@ -440,6 +440,88 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_mixed(DevScene sc, DevEnds e
           break;
       }
       s = oe;
+    }
+  }
+}
+
+// ----------------------------------------------------- visibility prescreen --
+// Candidates queued for refinement whose FP32 solution is well converged
+// (cost < 1e-10) and has a segment that crosses an occluder rectangle with a
+// clearance of CLEAR_M on every side (both ends CLEAR_M off the plane, the
+// crossing CLEAR_M inside the rectangle) are certainly blocked after
+// refinement too (the refinement moves a converged point by orders of
+// magnitude less), so they are rejected here; the others go to the second
+// list that k_refine processes.  Paraboloid occluders never reject here.
+constexpr float CLEAR_M = 0.25f;
+constexpr float PRESCREEN_VIS_COST = 1e-10f;
+
+__device__ __forceinline__ bool clearly_blocked(const DevScene& sc, const v3<float>& A, const v3<float>& B) {
+  for (int o = 0; o < sc.n_occ; ++o) {
+    if (__ldg(sc.occ_kind + o) != 0) continue;
+    const float4 f0 = __ldg(sc.c32 + o), f1 = __ldg(sc.c32 + sc.n_occ + o), f2 = __ldg(sc.c32 + 2 * sc.n_occ + o),
+                 f3 = __ldg(sc.c32 + 3 * sc.n_occ + o);
+    const v3<float> O = mk(f0.x, f0.y, f0.z), n = mk(f3.x, f3.y, f3.z);
+    const float sA = dot(A - O, n), sB = dot(B - O, n);
+    if (!((sA > CLEAR_M && sB < -CLEAR_M) || (sA < -CLEAR_M && sB > CLEAR_M))) continue;
+    const float t = sA / (sA - sB);
+    const v3<float> P = axpy(t, B - A, A) - O;
+    const float uu = dot(P, mk(f1.x, f1.y, f1.z)), vv = dot(P, mk(f2.x, f2.y, f2.z));
+    if (uu > CLEAR_M && uu < f0.w - CLEAR_M && vv > CLEAR_M && vv < f1.w - CLEAR_M) return true;
+  }
+  return false;
+}
+
+template <int N>
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevEnds ep, const float4* ends32,
+                                                               CandView cv, SolView out, RefineList rl1,
+                                                               RefineList rl2) {
+  int64_t end = cv.order_begin[N];
+  if (end > cv.cap) end = cv.cap;
+  int64_t begin = cv.order_begin[N - 1];
+  if (begin > end) begin = end;
+  int64_t n = (int64_t)rl1.count[N - 1];
+  if (n > end - begin) n = end - begin;
+  const unsigned lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+    const int64_t i = i0 + threadIdx.x;
+    bool keep = false;
+    int64_t c = 0;
+    if (i < n) {
+      c = begin + rl1.idx[begin + i];
+      if (c >= begin && c < end) {
+        keep = true;
+        if (out.cost[c] < (double)PRESCREEN_VIS_COST) {
+          const Cand cd = decode(__ldg(cv.rec + c));
+          int it_, ir_;
+          pair_ends(ep, cd.pair, it_, ir_);
+          v3<float> P[N + 2];
+          P[0] = load_end<float>(ep.tx, ends32, it_);
+          P[N + 1] = load_end<float>(ep.rx, ends32 + ep.n_tx, ir_);
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const int kind = __ldg(sc.kind + cd.ids[k]);
+            const Rec<float> r = load_obj32(sc, cd.ids[k]);
+            P[k + 1] = point_at<float, false>(kind, r, d2f_bits(out.T[(int64_t)(2 * k) * out.cap + c]),
+                                              d2f_bits(out.T[(int64_t)(2 * k + 1) * out.cap + c])).X;
+          }
+          bool blocked = false;
+#pragma unroll
+          for (int j = 0; j <= N; ++j) blocked = blocked || clearly_blocked(sc, P[j], P[j + 1]);
+          if (blocked) {
+            out.status[c] = (uint8_t)(out.status[c] | MPT_PATH_PRESCREENED);
+            keep = false;
+          }
+        }
+      }
+    }
+    const unsigned km = __ballot_sync(FULL, keep);
+    if (km) {
+      const int leader = __ffs(km) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(rl2.count + (N - 1), (unsigned long long)__popc(km));
+      base = __shfl_sync(FULL, base, leader);
+      if (keep) rl2.idx[begin + (int64_t)base + __popc(km & ((1u << lane) - 1u))] = (int32_t)(c - begin);
     }
   }
 }
@@ -522,7 +604,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_refine(DevScene sc, DevEnds ep,
       cholesky<Q, float>(jtj, cfg.mu32);
       chol_solve<Q, float>(jtj, g, dlt);
 #pragma unroll
-      for (int j = 0; j < Q; ++j) T[j] += (double)dlt[j];
+      for (int j = 0; j < Q; ++j) T[j] += f2d_bits(dlt[j]);
       c64 = eval_path<N, double, float, true>(kind, rec, T, A, B, jtj, g, ok);
     }
     if (!ok || !(c64 < 1e-24)) {
@@ -558,17 +640,23 @@ static int grid_for(mpt_ctx* ctx, K kernel, const mpt_schedule* sch) {
 template <int PREC>
 static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, const float4* ends32, const CandView& cv,
                        const SolView& sv, const SolveCfg& cfg, const mpt_schedule* sch, RefineList rl,
-                       cudaStream_t st) {
-  // counters[0..3]: per-order candidate cursors; counters[8..11]: refine list sizes
+                       RefineList rl2, bool curved, cudaStream_t st) {
+  // counters[0..3]: per-order candidate cursors; [4]: mixed-order cursor;
+  // [8..11]: refine list sizes; [12..15]: sizes after the visibility prescreen
   MPT_CUDA_TRY(cudaMemsetAsync(ctx->counters, 0, 16 * sizeof(unsigned long long), st));
   if (sch && sch->mixed_orders) {
     k_gn_mixed<PREC><<<grid_for(ctx, k_gn_mixed<PREC>, sch), SOLVE_BLOCK, 0, st>>>(sc, ep, ends32, cv, sv, cfg,
                                                                                   ctx->counters + 4, rl);
     MPT_LAUNCH_CHECK();
   } else {
-#define MPT_LAUNCH_GN(N)                                                                             \
-  k_gn<N, PREC><<<grid_for(ctx, k_gn<N, PREC>, sch), SOLVE_BLOCK, 0, st>>>(sc, ep, ends32, cv, sv, cfg,      \
-                                                                          ctx->counters + (N - 1), rl); \
+    // scenes made of planes and straight edges get the smaller solver
+#define MPT_LAUNCH_GN(N)                                                                                     \
+  if (curved)                                                                                                \
+    k_gn<N, PREC, true><<<grid_for(ctx, k_gn<N, PREC, true>, sch), SOLVE_BLOCK, 0, st>>>(                    \
+        sc, ep, ends32, cv, sv, cfg, ctx->counters + (N - 1), rl);                                           \
+  else                                                                                                       \
+    k_gn<N, PREC, false><<<grid_for(ctx, k_gn<N, PREC, false>, sch), SOLVE_BLOCK, 0, st>>>(                  \
+        sc, ep, ends32, cv, sv, cfg, ctx->counters + (N - 1), rl);                                           \
   MPT_LAUNCH_CHECK();
   MPT_LAUNCH_GN(1)
   MPT_LAUNCH_GN(2)
@@ -577,8 +665,17 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
 #undef MPT_LAUNCH_GN
   }
   if (PREC == MPT_FP32_FP64REFINE) {
-#define MPT_LAUNCH_REF(N)                                                                               \
-  k_refine<N><<<grid_for(ctx, k_refine<N>, nullptr), SOLVE_BLOCK, 0, st>>>(sc, ep, cv, sv, cfg, rl); \
+#define MPT_LAUNCH_VIS(N)                                                                                \
+  k_vis_prescreen<N><<<grid_for(ctx, k_vis_prescreen<N>, nullptr), SOLVE_BLOCK, 0, st>>>(sc, ep, ends32, cv, \
+                                                                                          sv, rl, rl2);     \
+  MPT_LAUNCH_CHECK();
+    MPT_LAUNCH_VIS(1)
+    MPT_LAUNCH_VIS(2)
+    MPT_LAUNCH_VIS(3)
+    MPT_LAUNCH_VIS(4)
+#undef MPT_LAUNCH_VIS
+#define MPT_LAUNCH_REF(N)                                                                                \
+  k_refine<N><<<grid_for(ctx, k_refine<N>, nullptr), SOLVE_BLOCK, 0, st>>>(sc, ep, cv, sv, cfg, rl2); \
   MPT_LAUNCH_CHECK();
     MPT_LAUNCH_REF(1)
     MPT_LAUNCH_REF(2)
@@ -615,8 +712,10 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
   SolView sv{out->T, out->cost, out->status, out->iters, out->evals, out->T32, out->capacity};
   DevEnds ep = dev_ends(ends);
   RefineList rl{ctx->counters + 8, nullptr};
+  RefineList rl2{ctx->counters + 12, nullptr};
   if (precision == MPT_FP32_FP64REFINE) {
-    const size_t need = (size_t)cand->capacity * sizeof(int32_t) + 256;
+    // two lists of one 4-byte position per candidate: queued, then kept
+    const size_t need = 2 * (size_t)cand->capacity * sizeof(int32_t) + 256;
     if (ctx->rscratch_bytes < need) {
       if (ctx->rscratch) MPT_CUDA_TRY(cudaFreeAsync(ctx->rscratch, st));
       ctx->rscratch = nullptr;
@@ -625,6 +724,7 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
       ctx->rscratch_bytes = need;
     }
     rl.idx = reinterpret_cast<int32_t*>(ctx->rscratch);
+    rl2.idx = rl.idx + cand->capacity;
   }
   // FP32 copies of the endpoints for the FP32 iterations
   const int n_ends = ends->n_tx + ends->n_rx;
@@ -641,11 +741,16 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
     k_ends_f32<<<(n_ends + 255) / 256, 256, 0, st>>>(ends->tx, ends->n_tx, ends->rx, ends->n_rx, ends32);
     MPT_LAUNCH_CHECK();
   }
+  bool curved = false;
+  for (int i = 0; i < scene->n_obj; ++i)
+    curved = curved || scene->host_kind[i] == MPT_PARABOLOID || scene->host_kind[i] == MPT_ARC_EDGE;
   switch (precision) {
-    case MPT_FP64_PLAIN: return launch_prec<MPT_FP64_PLAIN>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, st);
-    case MPT_FP32: return launch_prec<MPT_FP32>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, st);
+    case MPT_FP64_PLAIN:
+      return launch_prec<MPT_FP64_PLAIN>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, st);
+    case MPT_FP32:
+      return launch_prec<MPT_FP32>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, st);
     case MPT_FP32_FP64REFINE:
-      return launch_prec<MPT_FP32_FP64REFINE>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, st);
+      return launch_prec<MPT_FP32_FP64REFINE>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, st);
     default: return MPT_ERR_ARG;
   }
 }

@@ -382,6 +382,51 @@ def test_adjoint_matches_oracle_gradient(mpt, ctx, name):
     print(f"adjoint {name}: {n} paths, |dL/dTX| {np.abs(wtx).max():.3e}")
 
 
+def test_autograd_function_matches_central_differences(mpt, ctx):
+    """MPT lengths as a torch.autograd.Function: d(sum of lengths)/d(RX, TX,
+    plane offsets) against central differences (h = 1e-4 m) of the GPU
+    forward, over the paths present in the base and both perturbed runs."""
+    from paper_2301_06399_gb300 import autograd as ag
+
+    sc = S.urban_block(4)
+    tx = torch.tensor(sc.tx, dtype=torch.float64, device="cuda", requires_grad=True)
+    rx = torch.tensor(sc.rx, dtype=torch.float64, device="cuda", requires_grad=True)
+    dd = torch.zeros(sc.n_obj, dtype=torch.float64, device="cuda", requires_grad=True)
+    L, X, cand = ag.path_lengths(ctx, sc, tx, rx, dd)
+    assert L.numel() > 100
+    h = 1e-4
+
+    def lengths(tx_, rx_, dd_):
+        with torch.no_grad():
+            l2, _, c2 = ag.path_lengths(ctx, sc, tx_, rx_, dd_)
+        return dict(zip(c2.cpu().tolist(), l2.cpu().tolist()))
+
+    base = dict(zip(cand.cpu().tolist(), L.detach().cpu().tolist()))
+    rng = np.random.default_rng(3)
+    checks = [("rx", int(rng.integers(sc.rx.shape[0])), int(rng.integers(3))) for _ in range(3)]
+    checks += [("tx", 0, j) for j in range(3)]
+    walls = [int(o) for o in rng.choice(np.nonzero(sc.obj_kind == 0)[0], 3, replace=False)]
+    checks += [("dd", o, 0) for o in walls]
+    for what, i, j in checks:
+        args_p = [tx.detach().clone(), rx.detach().clone(), dd.detach().clone()]
+        args_m = [tx.detach().clone(), rx.detach().clone(), dd.detach().clone()]
+        k = {"tx": 0, "rx": 1, "dd": 2}[what]
+        if what == "dd":
+            args_p[k][i] += h
+            args_m[k][i] -= h
+        else:
+            args_p[k][i, j] += h
+            args_m[k][i, j] -= h
+        lp, lm = lengths(*args_p), lengths(*args_m)
+        common = sorted(set(base) & set(lp) & set(lm))
+        fd = sum((lp[c] - lm[c]) / (2 * h) for c in common)
+        mask = torch.tensor([1.0 if int(c) in set(common) else 0.0 for c in cand.cpu().tolist()],
+                            dtype=torch.float64, device="cuda")
+        g = torch.autograd.grad(L, [tx, rx, dd], grad_outputs=mask, retain_graph=True)
+        ad = g[k][i].item() if what == "dd" else g[k][i, j].item()
+        assert abs(ad - fd) < 1e-5 * max(1.0, abs(fd)), (what, i, j, ad, fd)
+
+
 # ---------------------------------------------------------- FP32 precision --
 def test_fp32_only_error_is_reported(mpt, ctx):
     """FP32 iterations alone reach ~1e-5..1e-3 m; the FP64 refinement brings
