@@ -246,6 +246,28 @@ int mpt_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
                  const mpt_candidates* cand, const mpt_solutions* sol, double tau, mpt_paths* out,
                  int64_t* d_valid_count, void* stream);
 
+/* mpt_validate without any device allocation.  The paper has no counterpart:
+ * this is a service for callers that cannot call cudaMalloc, such as
+ * processes whose device memory is reserved up front by their own memory
+ * manager (where one more allocation fails or breaks up the pool) and loops
+ * that must not wait on the driver's allocator.  Same arguments, results and
+ * errors as mpt_validate, but the call's scratch is one array in the
+ * library's device data (about 2.9 MB, present on every GPU that loads the
+ * library until the process exits) instead of context memory grown on demand:
+ *   - cand->capacity may be at most 2^24 (16,777,216) candidates; larger
+ *     requests return MPT_ERR_CAPACITY before anything is enqueued;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device made current for the lookup);
+ *     make that first call before any stream capture;
+ *   - the call allocates nothing (no cudaMalloc, cudaFree or allocating
+ *     library routine);
+ *   - every call uses the same array, which keeps the previous call's
+ *     contents (the call overwrites every word it reads): calls that
+ *     overlap on the GPU, from two streams or two host threads, race. */
+int mpt_validate_noalloc(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
+                         const mpt_candidates* cand, const mpt_solutions* sol, double tau, mpt_paths* out,
+                         int64_t* d_valid_count, void* stream);
+
 /* Reads (synchronously) and clears the context's device error flag: MPT_OK or
  * MPT_ERR_TIMEOUT when a bounded device wait gave up since the last check. */
 int mpt_ctx_check(mpt_ctx* ctx, void* stream);

@@ -12,6 +12,8 @@
 //              per block.
 //   k_scan     one CTA: exclusive scan of the block counts, total count.
 //   k_scatter  writes each valid path at (block offset + rank in block).
+#include <mutex>
+
 #include "mpt_internal.cuh"
 
 namespace mpt {
@@ -397,4 +399,86 @@ int launch_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* e
   return MPT_OK;
 }
 
+// --------------------------------------------- validation without allocation --
+// Scratch of mpt_validate_noalloc: one fixed array in the library's device
+// data, present on every GPU that loads the library until the process exits.
+// It serves up to NOALLOC_MAX_CANDIDATES candidates (2^24): per block of 256
+// candidates one 8-byte offset, one 4-byte count and eight 4-byte ballots,
+// 2.9 MB in all.  Every word a call reads is written earlier in the same call
+// (k_accept writes the count and ballots of every block it covers, k_scan
+// every offset), so nothing needs clearing between calls; calls that overlap
+// on the GPU (two streams, two host threads) race on the array.
+constexpr int64_t NOALLOC_MAX_CANDIDATES = int64_t(1) << 24;
+constexpr int64_t NOALLOC_MAX_BLOCKS = NOALLOC_MAX_CANDIDATES / ACC_BLOCK;
+constexpr size_t NOALLOC_BYTES = (size_t)NOALLOC_MAX_BLOCKS * (8 + 4 + 4 * ACC_WARPS);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Device address of g_noalloc_scratch on `device`, looked up once per device
+// with that device current.  In host code the array's name only stands for
+// the symbol; passing it to a kernel would not give its device address.
+static int noalloc_scratch(int device, unsigned char** out) {
+  static std::mutex mu;
+  static void* addr[256] = {};
+  if (device < 0 || device >= 256) return MPT_ERR_ARG;
+  std::lock_guard<std::mutex> lock(mu);
+  if (addr[device] == nullptr) {
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return MPT_ERR_CUDA;
+    if (prev != device && cudaSetDevice(device) != cudaSuccess) return MPT_ERR_CUDA;
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (prev != device) cudaSetDevice(prev);
+    if (e != cudaSuccess || p == nullptr) {
+      std::fprintf(stderr, "libmpt: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+      return MPT_ERR_CUDA;
+    }
+    addr[device] = p;
+  }
+  *out = reinterpret_cast<unsigned char*>(addr[device]);
+  return MPT_OK;
+}
+
+static int launch_validate_noalloc(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
+                                   const mpt_candidates* cand, const mpt_solutions* sol, double tau,
+                                   mpt_paths* out, int64_t* d_valid_count, cudaStream_t st) {
+  const int64_t cap = cand->capacity;
+  if (cap > NOALLOC_MAX_CANDIDATES) return MPT_ERR_CAPACITY;
+  const int64_t n_blocks = (cap + ACC_BLOCK - 1) / ACC_BLOCK;
+  if (n_blocks < 1) return MPT_OK;
+  unsigned char* base = nullptr;
+  const int rc = noalloc_scratch(ctx->device, &base);
+  if (rc != MPT_OK) return rc;
+  ScratchView sv;
+  sv.blk_off = reinterpret_cast<int64_t*>(base);
+  sv.blk_count = reinterpret_cast<uint32_t*>(base + (size_t)NOALLOC_MAX_BLOCKS * 8);
+  sv.ballots = reinterpret_cast<uint32_t*>(base + (size_t)NOALLOC_MAX_BLOCKS * 12);
+  AccView av{reinterpret_cast<const uint4*>(cand->rec), cand->count, cap, sol->T, sol->cost, sol->status,
+             sol->capacity};
+  const DevEnds ep = dev_ends(ends);
+  const size_t smem = (size_t)scene->d.n_occ * 64;
+  if (smem > 48 * 1024) {
+    cudaFuncSetAttribute(k_accept, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  k_accept<<<(unsigned)n_blocks, ACC_BLOCK, smem, st>>>(scene->d, ep, av, tau, sv, ctx->err_flag);
+  MPT_LAUNCH_CHECK();
+  k_scan<<<1, 1024, 0, st>>>(sv.blk_count, n_blocks, sv.blk_off, d_valid_count);
+  MPT_LAUNCH_CHECK();
+  PathView pv{out->cand, out->X, out->T, out->length, out->cost, out->capacity};
+  k_scatter<<<(unsigned)n_blocks, ACC_BLOCK, 0, st>>>(scene->d, ep, av, sv, pv);
+  MPT_LAUNCH_CHECK();
+  return MPT_OK;
+}
+
 }  // namespace mpt
+
+extern "C" int mpt_validate_noalloc(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
+                                    const mpt_candidates* cand, const mpt_solutions* sol, double tau,
+                                    mpt_paths* out, int64_t* d_valid_count, void* stream) {
+  if (!ctx || !scene || !cand || !sol || !out || !d_valid_count || !cand->rec || !cand->count || !sol->T ||
+      !sol->cost || !sol->status || !out->cand || !out->X || !out->T || !out->length || !out->cost)
+    return MPT_ERR_ARG;
+  if (mpt::check_ends(ends) != MPT_OK) return MPT_ERR_ARG;
+  if (!(tau > 0) || out->capacity < 0 || sol->capacity < cand->capacity) return MPT_ERR_ARG;
+  return mpt::launch_validate_noalloc(ctx, scene, ends, cand, sol, tau, out, d_valid_count,
+                                      reinterpret_cast<cudaStream_t>(stream));
+}

@@ -62,7 +62,7 @@ _lock = threading.Lock()
 # Every symbol include/mpt.h declares.
 SYMBOLS = ["mpt_ctx_create", "mpt_ctx_destroy", "mpt_ctx_sm_count", "mpt_ctx_check", "mpt_scene_upload",
            "mpt_scene_free", "mpt_enumerate", "mpt_candidate_count", "mpt_solve", "mpt_validate", "mpt_grad",
-           "mpt_status_string", "mpt_flop_model"]
+           "mpt_status_string", "mpt_flop_model", "mpt_validate_noalloc"]
 
 
 def library_path() -> str:
@@ -92,6 +92,8 @@ def lib():
                                     C.POINTER(Schedule), C.POINTER(SolStruct), P]
             L.mpt_validate.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct), C.POINTER(SolStruct),
                                        D, C.POINTER(PathStruct), P, P]
+            L.mpt_validate_noalloc.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct),
+                                               C.POINTER(SolStruct), D, C.POINTER(PathStruct), P, P]
             L.mpt_grad.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct), C.POINTER(PathStruct), P,
                                    P, P, P, P, P, P]
             L.mpt_status_string.restype = C.c_char_p
