@@ -190,11 +190,48 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
       if (same) { obj_occ[o] = q; break; }
     }
   }
+  // occluder bounding boxes from FP64 corners, grown by 1 cm: rectangles from
+  // their four corners, paraboloid patches from the eight corners of the
+  // local box [-rho, rho]^2 x [0, rho^2 / (4f)] that holds the patch
+  std::vector<float> cbox((size_t)nc * 8, 0.f);
+  for (int q = 0; q < nc; ++q) {
+    const double* v = &cv[(size_t)16 * q];
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    auto add = [&](const double* p) {
+      for (int j = 0; j < 3; ++j) {
+        lo[j] = std::fmin(lo[j], p[j]);
+        hi[j] = std::fmax(hi[j], p[j]);
+      }
+    };
+    if (desc->occ_kind[q] == MPT_OCC_RECT) {
+      for (int a = 0; a < 2; ++a)
+        for (int c = 0; c < 2; ++c) {
+          double p[3];
+          for (int j = 0; j < 3; ++j) p[j] = v[j] + a * v[3] * v[4 + j] + c * v[7] * v[8 + j];
+          add(p);
+        }
+    } else {
+      const double rho = v[13], zmax = rho * rho * v[12];
+      for (int a = 0; a < 2; ++a)
+        for (int c = 0; c < 2; ++c)
+          for (int z = 0; z < 2; ++z) {
+            const double sx = a ? rho : -rho, sy = c ? rho : -rho, sz = z ? zmax : 0.0;
+            const double t0[3] = {v[3], v[7], v[11]};
+            double p[3];
+            for (int j = 0; j < 3; ++j) p[j] = t0[j] + sx * v[j] + sy * v[4 + j] + sz * v[8 + j];
+            add(p);
+          }
+    }
+    for (int j = 0; j < 3; ++j) {
+      cbox[(size_t)4 * q + j] = (float)(lo[j] - 0.01);
+      cbox[(size_t)4 * (nc + q) + j] = (float)(hi[j] + 0.01);
+    }
+  }
   const size_t s_kind = align256((size_t)no * 4), s_o32 = align256((size_t)no * 64),
                s_o64 = align256((size_t)no * 128), s_ck = align256((size_t)nc * 4 + 4),
                s_c32 = align256((size_t)nc * 64 + 16), s_c64 = align256((size_t)nc * 128 + 16),
-               s_oo = align256((size_t)no * 4);
-  const size_t total = s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo;
+               s_oo = align256((size_t)no * 4), s_cb = align256((size_t)nc * 32 + 16);
+  const size_t total = s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb;
   MPT_CUDA_TRY(cudaSetDevice(ctx->device));
   void* mem = nullptr;
   MPT_CUDA_TRY(cudaMalloc(&mem, total));
@@ -222,6 +259,7 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   d.c32 = reinterpret_cast<const float4*>(put(c32.data(), (size_t)nc * 64, s_c32));
   d.c64 = reinterpret_cast<const double2*>(put(c64.data(), (size_t)nc * 128, s_c64));
   d.obj_occ = reinterpret_cast<const int32_t*>(put(obj_occ.data(), (size_t)no * 4, s_oo));
+  d.cbox = reinterpret_cast<const float4*>(put(cbox.data(), (size_t)nc * 32, s_cb));
   d.scale = desc->scale;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -24,8 +24,17 @@ struct DevScene {
   const float4* c32;        // [4][n_occ]
   const double2* c64;       // [8][n_occ]
   const int32_t* obj_occ;   // [n_obj]: occluder holding this plane's rectangle, or -1
+  const float4* cbox;       // [2][n_occ]: occluder bounding boxes (lo, hi), grown by 1 cm
   double scale;
 };
+
+// A segment can only meet an occluder whose box its own box overlaps (the
+// boxes are grown by 1 cm at upload, far above FP32 rounding of the ends).
+__device__ __forceinline__ bool box_overlap(const float4& lo, const float4& hi, const v3<float>& A,
+                                            const v3<float>& B) {
+  return fminf(A.x, B.x) <= hi.x && fmaxf(A.x, B.x) >= lo.x && fminf(A.y, B.y) <= hi.y &&
+         fmaxf(A.y, B.y) >= lo.y && fminf(A.z, B.z) <= hi.z && fmaxf(A.z, B.z) >= lo.z;
+}
 
 struct DevEnds {
   const double* tx;

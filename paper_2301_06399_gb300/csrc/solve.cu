@@ -458,6 +458,7 @@ constexpr float PRESCREEN_VIS_COST = 1e-10f;
 __device__ __forceinline__ bool clearly_blocked(const DevScene& sc, const v3<float>& A, const v3<float>& B) {
   for (int o = 0; o < sc.n_occ; ++o) {
     if (__ldg(sc.occ_kind + o) != 0) continue;
+    if (!box_overlap(__ldg(sc.cbox + o), __ldg(sc.cbox + sc.n_occ + o), A, B)) continue;
     const float4 f0 = __ldg(sc.c32 + o), f1 = __ldg(sc.c32 + sc.n_occ + o), f2 = __ldg(sc.c32 + 2 * sc.n_occ + o),
                  f3 = __ldg(sc.c32 + 3 * sc.n_occ + o);
     const v3<float> O = mk(f0.x, f0.y, f0.z), n = mk(f3.x, f3.y, f3.z);

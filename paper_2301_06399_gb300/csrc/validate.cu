@@ -191,6 +191,7 @@ __device__ bool accept_one(const DevScene& sc, const DevEnds& ep, const Cand& cd
     const int own1 = j < N ? sc.obj_occ[cd.ids[j]] : -1;
     for (int o = 0; o < sc.n_occ; ++o) {
       if (o == own0 || o == own1) continue;
+      if (!box_overlap(occ_sm[4 * sc.n_occ + o], occ_sm[5 * sc.n_occ + o], Af, Bf)) continue;
       int b;
       if (sc.occ_kind[o] == 0) {
         b = rect32(occ_sm, sc.n_occ, o, Af, Bf);
@@ -217,9 +218,13 @@ __global__ void __launch_bounds__(ACC_BLOCK) k_accept(DevScene sc, DevEnds ep, A
   }
   __syncthreads();
   if (threadIdx.x == 0 && sc.n_occ > 0) {
-    mbar_expect_tx(&bar, 4u * field_bytes);
+    // fields 0-3: FP32 occluder records; 4-5: their boxes (lo, hi)
+    mbar_expect_tx(&bar, 6u * field_bytes);
 #pragma unroll
     for (int f = 0; f < 4; ++f) bulk_g2s(occ_sm + f * sc.n_occ, sc.c32 + f * sc.n_occ, field_bytes, &bar);
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
+      bulk_g2s(occ_sm + (4 + f) * sc.n_occ, sc.cbox + f * sc.n_occ, field_bytes, &bar);
   }
   // bounded wait for the staged occluders
   bool staged = true;
@@ -385,7 +390,7 @@ int launch_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* e
   AccView av{reinterpret_cast<const uint4*>(cand->rec), cand->count, cap, sol->T, sol->cost, sol->status,
              sol->capacity};
   const DevEnds ep = dev_ends(ends);
-  const size_t smem = (size_t)scene->d.n_occ * 64;
+  const size_t smem = (size_t)scene->d.n_occ * 96;
   if (smem > 48 * 1024) {
     cudaFuncSetAttribute(k_accept, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
@@ -455,7 +460,7 @@ static int launch_validate_noalloc(mpt_ctx* ctx, const mpt_scene* scene, const m
   AccView av{reinterpret_cast<const uint4*>(cand->rec), cand->count, cap, sol->T, sol->cost, sol->status,
              sol->capacity};
   const DevEnds ep = dev_ends(ends);
-  const size_t smem = (size_t)scene->d.n_occ * 64;
+  const size_t smem = (size_t)scene->d.n_occ * 96;
   if (smem > 48 * 1024) {
     cudaFuncSetAttribute(k_accept, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
