@@ -356,7 +356,7 @@ def run_ours(args):
                      "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {SM_MAX_MHZ_NOMINAL:.0f} MHz (derived)",
                      "solve_ms": solve_avg_ms, "fp32_flops_per_launch": flops,
-                     "traffic": profile_traffic("k_solve<2,refine>")},
+                     "traffic": profile_traffic("mpt_solve")},
         "fp64_plain": {"ms_per_step": float(np.median(fp64_ms)),
                        "value": n_cand * ws / (float(np.median(fp64_ms)) * 1e-3), "unit": UNIT,
                        "valid_paths_per_step": n_valid_fp64},
