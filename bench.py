@@ -240,8 +240,9 @@ def run_ours(args):
         n_valid = paths.n()
         flops = algorithmic_flops(mpt, sc, cands, sols, n_cand)
         # enumerate (2) + solve (endpoint copy, 4 orders x {solver, visibility
-        # prescreen, refinement}) + validate (3) + adjoint (1)
-        launches_per_step = 2 + (1 + 4 * 3) + 3 + 1
+        # prescreen, refinement}) + validate (list, test, scan, scatter, fill) +
+        # adjoint (one launch per order)
+        launches_per_step = 2 + (1 + 4 * 3) + 5 + 4
 
         # ---- device-resident timing
         ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))

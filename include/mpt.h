@@ -239,9 +239,11 @@ int mpt_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
  * occluder (Sec. II: bounds applied a posteriori).  Valid paths are written in
  * candidate order to `out`; the number of valid paths goes to *d_valid_count
  * (device int64).  If it exceeds out->capacity, only the first capacity paths
- * are written and the full count is still reported.  Occluders are staged in
- * shared memory with bulk asynchronous copies; a bounded wait on that copy
- * that gives up sets the context's error flag (see mpt_ctx_check). */
+ * are written and the full count is still reported.  cand->capacity must be
+ * below 2^32 - 1 (candidate indices are listed in 32 bits; MPT_ERR_CAPACITY
+ * otherwise).  Occluders are staged in shared memory with bulk asynchronous
+ * copies; a bounded wait on that copy that gives up sets the context's error
+ * flag (see mpt_ctx_check). */
 int mpt_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
                  const mpt_candidates* cand, const mpt_solutions* sol, double tau, mpt_paths* out,
                  int64_t* d_valid_count, void* stream);
@@ -252,7 +254,7 @@ int mpt_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
  * manager (where one more allocation fails or breaks up the pool) and loops
  * that must not wait on the driver's allocator.  Same arguments, results and
  * errors as mpt_validate, but the call's scratch is one array in the
- * library's device data (about 2.9 MB, present on every GPU that loads the
+ * library's device data (about 3.3 MB, present on every GPU that loads the
  * library until the process exits) instead of context memory grown on demand:
  *   - cand->capacity may be at most 2^24 (16,777,216) candidates; larger
  *     requests return MPT_ERR_CAPACITY before anything is enqueued;

@@ -39,9 +39,17 @@ struct Inter {
   }
 };
 
+// Contributions of one path, added to the outputs by the caller.
 template <int N>
-__device__ void grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, const double* Tc, double gL,
-                         const double* gX, double* g_tx, double* g_rx, double* g_obj) {
+struct GradOut {
+  int it, ir;
+  double tx[3], rx[3];
+  double obj[N];  // d/d offset of plane ids[m]; 0 for other kinds
+};
+
+template <int N>
+__device__ bool grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, const double* Tc, double gL,
+                         const double* gX, bool want_tx, bool want_rx, bool want_obj, GradOut<N>& o) {
   constexpr int Q = 2 * N;
   int it_, ir_;
   pair_ends(ep, cd.pair, it_, ir_);
@@ -64,7 +72,7 @@ __device__ void grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, 
 #pragma unroll
   for (int k = 0; k < N; ++k)
     if (is_edge(kind[k])) jtj[tri(2 * k + 1, 2 * k + 1)] = 1.0;
-  if (!cholesky<Q, double>(jtj, 0.0)) return;
+  if (!cholesky<Q, double>(jtj, 0.0)) return false;
   // geometry
   PointT<double> pt[N];
 #pragma unroll
@@ -142,28 +150,25 @@ __device__ void grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, 
     }
     z[k] = r;
   }
+  o.it = it_;
+  o.ir = ir_;
   // TX: a displacement of X_0 enters interaction 0 as "previous point"
-  if (g_tx) {
+  if (want_tx) {
     const v3<double> ex = mk(1.0, 0.0, 0.0), ey = mk(0.0, 1.0, 0.0), ez = mk(0.0, 0.0, 1.0);
-    const double gx = -gL * u[0].x - dot(z[0], in[0].prev(ex));
-    const double gy = -gL * u[0].y - dot(z[0], in[0].prev(ey));
-    const double gz = -gL * u[0].z - dot(z[0], in[0].prev(ez));
-    atomicAdd(g_tx + 3 * it_, gx);
-    atomicAdd(g_tx + 3 * it_ + 1, gy);
-    atomicAdd(g_tx + 3 * it_ + 2, gz);
+    o.tx[0] = -gL * u[0].x - dot(z[0], in[0].prev(ex));
+    o.tx[1] = -gL * u[0].y - dot(z[0], in[0].prev(ey));
+    o.tx[2] = -gL * u[0].z - dot(z[0], in[0].prev(ez));
   }
-  if (g_rx) {
+  if (want_rx) {
     const v3<double> ex = mk(1.0, 0.0, 0.0), ey = mk(0.0, 1.0, 0.0), ez = mk(0.0, 0.0, 1.0);
-    const double gx = gL * u[N].x - dot(z[N - 1], in[N - 1].next(ex));
-    const double gy = gL * u[N].y - dot(z[N - 1], in[N - 1].next(ey));
-    const double gz = gL * u[N].z - dot(z[N - 1], in[N - 1].next(ez));
-    atomicAdd(g_rx + 3 * ir_, gx);
-    atomicAdd(g_rx + 3 * ir_ + 1, gy);
-    atomicAdd(g_rx + 3 * ir_ + 2, gz);
+    o.rx[0] = gL * u[N].x - dot(z[N - 1], in[N - 1].next(ex));
+    o.rx[1] = gL * u[N].y - dot(z[N - 1], in[N - 1].next(ey));
+    o.rx[2] = gL * u[N].z - dot(z[N - 1], in[N - 1].next(ez));
   }
-  if (g_obj) {
+  if (want_obj) {
 #pragma unroll
     for (int m = 0; m < N; ++m) {
+      o.obj[m] = 0.0;
       if (kind[m] != K_PLANE) continue;
       const v3<double> n = rec[m].f3(12);
       double gd = gL * dot(u[m] - u[m + 1], n);
@@ -171,8 +176,33 @@ __device__ void grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, 
       gd -= dot(z[m], in[m].self(n));
       if (m >= 1) gd -= dot(z[m - 1], in[m - 1].next(n));
       if (m + 1 < N) gd -= dot(z[m + 1], in[m + 1].prev(n));
-      atomicAdd(g_obj + cd.ids[m], gd);
+      o.obj[m] = gd;
     }
+  }
+  return true;
+}
+
+// Adds v (W values) at dst + W * key for the lanes with `have`.  When every
+// such lane of the warp has the same key (one TX; the objects of one
+// sequence), the warp sums first and one lane adds; otherwise each lane adds.
+template <int W>
+__device__ __forceinline__ void warp_add(double* dst, bool have, int key, const double (&v)[W]) {
+  const unsigned act = __ballot_sync(0xffffffffu, have);
+  if (act == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(act) - 1;
+  const int k0 = __shfl_sync(0xffffffffu, key, leader);
+  if (__all_sync(0xffffffffu, !have || key == k0)) {
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      double a = have ? v[j] : 0.0;
+#pragma unroll
+      for (int d = 16; d >= 1; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+      if (lane == leader) atomicAdd(dst + (int64_t)W * k0 + j, a);
+    }
+  } else if (have) {
+#pragma unroll
+    for (int j = 0; j < W; ++j) atomicAdd(dst + (int64_t)W * key + j, v[j]);
   }
 }
 
@@ -187,32 +217,51 @@ struct GradView {
   const double* g_pts;
 };
 
+// One launch per path order: every launch scans all paths and takes those of
+// its order (valid paths come sorted by candidate, hence by order, so the
+// lanes of a warp agree), and each order gets registers of its own.  The
+// loop bounds are uniform over the block so that whole warps reach the
+// aggregated atomics together.
+template <int N>
 __global__ void __launch_bounds__(GRAD_BLOCK) k_grad(DevScene sc, DevEnds ep, GradView gv, double* g_tx,
                                                      double* g_rx, double* g_obj) {
   int64_t n = *gv.count;
   if (n > gv.pcap) n = gv.pcap;
-  for (int64_t i = (int64_t)blockIdx.x * GRAD_BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * GRAD_BLOCK) {
-    const int64_t c = gv.pcand[i];
-    if (c < 0 || c >= gv.rec_cap) continue;
-    const Cand cd = decode(gv.rec[c]);
-    if (!cand_in_range(sc, ep, cd)) continue;
-    double Tc[8];
+  for (int64_t i0 = (int64_t)blockIdx.x * GRAD_BLOCK; i0 < n; i0 += (int64_t)gridDim.x * GRAD_BLOCK) {
+    const int64_t i = i0 + threadIdx.x;
+    bool have = false;
+    GradOut<N> o;
+    Cand cd;
+    cd.order = 0;
+    if (i < n) {
+      const int64_t c = gv.pcand[i];
+      if (c >= 0 && c < gv.rec_cap) {
+        cd = decode(gv.rec[c]);
+        if (cd.order == N && cand_in_range(sc, ep, cd)) {
+          double Tc[2 * N];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) Tc[j] = gv.pT[(int64_t)j * gv.pcap + i];
-    double gX[12];
-    const double* gxp = nullptr;
-    if (gv.g_pts) {
+          for (int j = 0; j < 2 * N; ++j) Tc[j] = gv.pT[(int64_t)j * gv.pcap + i];
+          double gX[3 * N];
+          const double* gxp = nullptr;
+          if (gv.g_pts) {
 #pragma unroll
-      for (int j = 0; j < 12; ++j) gX[j] = gv.g_pts[(int64_t)j * gv.pcap + i];
-      gxp = gX;
+            for (int j = 0; j < 3 * N; ++j) gX[j] = gv.g_pts[(int64_t)j * gv.pcap + i];
+            gxp = gX;
+          }
+          have = grad_one<N>(sc, ep, cd, Tc, gv.g_len[i], gxp, g_tx != nullptr, g_rx != nullptr,
+                             g_obj != nullptr, o);
+        }
+      }
     }
-    const double gL = gv.g_len[i];
-    switch (cd.order) {
-      case 1: grad_one<1>(sc, ep, cd, Tc, gL, gxp, g_tx, g_rx, g_obj); break;
-      case 2: grad_one<2>(sc, ep, cd, Tc, gL, gxp, g_tx, g_rx, g_obj); break;
-      case 3: grad_one<3>(sc, ep, cd, Tc, gL, gxp, g_tx, g_rx, g_obj); break;
-      case 4: grad_one<4>(sc, ep, cd, Tc, gL, gxp, g_tx, g_rx, g_obj); break;
-      default: break;
+    if (__ballot_sync(0xffffffffu, have) == 0) continue;
+    if (g_tx) warp_add<3>(g_tx, have, o.it, o.tx);
+    if (g_rx) warp_add<3>(g_rx, have, o.ir, o.rx);
+    if (g_obj) {
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        const double v[1] = {o.obj[m]};
+        warp_add<1>(g_obj, have && o.obj[m] != 0.0, have ? cd.ids[m] : 0, v);
+      }
     }
   }
 }
@@ -226,7 +275,14 @@ int launch_grad(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
   int64_t blocks = (paths->capacity + GRAD_BLOCK - 1) / GRAD_BLOCK;
   const int64_t lim = (int64_t)ctx->sms * 8;
   if (blocks > lim) blocks = lim;
-  k_grad<<<(unsigned)blocks, GRAD_BLOCK, 0, st>>>(scene->d, dev_ends(ends), gv, g_tx, g_rx, g_obj);
+  const DevEnds ep = dev_ends(ends);
+  k_grad<1><<<(unsigned)blocks, GRAD_BLOCK, 0, st>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
+  MPT_LAUNCH_CHECK();
+  k_grad<2><<<(unsigned)blocks, GRAD_BLOCK, 0, st>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
+  MPT_LAUNCH_CHECK();
+  k_grad<3><<<(unsigned)blocks, GRAD_BLOCK, 0, st>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
+  MPT_LAUNCH_CHECK();
+  k_grad<4><<<(unsigned)blocks, GRAD_BLOCK, 0, st>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
   MPT_LAUNCH_CHECK();
   return MPT_OK;
 }

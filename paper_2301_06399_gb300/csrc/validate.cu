@@ -1,17 +1,25 @@
 // Acceptance of Algorithm 1 ("C < threshold and X is valid") and the union
 // of the valid paths into S, as a compacted list in candidate order.
 //
-//   k_accept   one thread per candidate: FP64 cost test, minimum segment
-//              length, bounds (Sec. II: bounds are applied a posteriori),
-//              then segment visibility against every occluder.  Occluder
-//              records are staged into shared memory by one bulk
-//              asynchronous copy per field array (cp.async.bulk completing
-//              on an mbarrier).  The test runs in FP32 with a 1 mm margin;
-//              decisions inside the margin are re-taken in FP64 with the
-//              exact rule.  Writes one ballot word per warp and one count
-//              per block.
-//   k_scan     one CTA: exclusive scan of the block counts, total count.
-//   k_scatter  writes each valid path at (block offset + rank in block).
+// Candidates are taken in groups of GROUP (2048) consecutive indices.
+//   k_flag         one block per group: lists the candidates that passed the
+//                  solver's FP64 stage with cost < tau (a few percent of them)
+//                  into a work list, one atomic per group.
+//   k_accept_list  one thread per listed candidate: minimum segment length,
+//                  bounds (Sec. II: bounds are applied a posteriori), then
+//                  segment visibility against every occluder.  Occluder
+//                  records and their boxes are staged into shared memory by
+//                  bulk asynchronous copies (cp.async.bulk completing on an
+//                  mbarrier).  The test runs in FP32 with a 1 mm margin;
+//                  decisions inside the margin are re-taken in FP64 with the
+//                  exact rule.  A valid candidate sets its bit in a bitmap
+//                  and counts itself in its group.
+//   k_accept_ovf   the same test for every candidate of a group whose
+//                  entries did not fit a bounded list (fixed-size scratch).
+//   k_scan         one CTA: exclusive scan of the group counts, total count.
+//   k_scatter      one warp per group: writes the index of each valid
+//                  candidate at (group offset + rank in group).
+//   k_fill         one thread per path: parameters, points, length, cost.
 #include <mutex>
 
 #include "mpt_internal.cuh"
@@ -35,11 +43,6 @@ struct AccView {
   int64_t sol_cap;
 };
 
-struct ScratchView {
-  uint32_t* ballots;   // [n_blocks * ACC_WARPS]
-  uint32_t* blk_count; // [n_blocks]
-  int64_t* blk_off;    // [n_blocks]
-};
 
 // ---------------------------------------------------------------- PTX ----
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -159,125 +162,290 @@ __device__ __forceinline__ bool in_bounds64(int kind, const Rec<double>& r, doub
   return phi <= r.v[11];
 }
 
+// Parameters clearly inside the bounds in FP32: away from every bound by
+// mb, which exceeds the FP32 rounding of the parameters and bounds (the
+// exact FP64 test decides everything else).  Arc edges always go to FP64.
+__device__ __forceinline__ bool clearly_in32(int kind, const Rec<float>& r, float s, float t, float mb) {
+  if (kind == K_PLANE) return s >= mb && s <= r.v[3] - mb && t >= mb && t <= r.v[7] - mb;
+  if (kind == K_PARAB) return r.v[13] > mb && s * s + t * t <= (r.v[13] - mb) * (r.v[13] - mb);
+  if (kind == K_LINE) return s >= r.v[3] + mb && s <= r.v[7] - mb;
+  return false;
+}
+
+// Point k (0 = TX, N + 1 = RX) of the path in FP64.
+template <int N>
+__device__ __forceinline__ v3<double> point64(const DevScene& sc, const DevEnds& ep, const Cand& cd, const double* Tc,
+                                              int it_, int ir_, int j) {
+  if (j == 0) return mk(ep.tx[3 * it_], ep.tx[3 * it_ + 1], ep.tx[3 * it_ + 2]);
+  if (j == N + 1) return mk(ep.rx[3 * ir_], ep.rx[3 * ir_ + 1], ep.rx[3 * ir_ + 2]);
+  const int k = j - 1;
+  return point_at<double, false>(sc.kind[cd.ids[k]], load_obj64(sc, cd.ids[k]), Tc[2 * k], Tc[2 * k + 1]).X;
+}
+
+// The acceptance rule, decided in FP32 wherever the FP32 values are clear of
+// the decision boundary by more than their rounding, else in FP64 with the
+// exact rule (the same rule as the FP64 CPU reference):
+//   bounds      clearly inside by mb = 1e-5 S + 4e-7 |bound| (FP32 parameters
+//               and points are within ~1e-6 relative of the FP64 values);
+//   segments    FP32 length >= 10 x the minimum length;
+//   visibility  FP32 test with a 1 mm margin (rect32).
 template <int N>
 __device__ bool accept_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, const double* Tc,
                            const float4* occ_sm, double S) {
   int it_, ir_;
   pair_ends(ep, cd.pair, it_, ir_);
-  v3<double> P[N + 2];
-  P[0] = mk(ep.tx[3 * it_], ep.tx[3 * it_ + 1], ep.tx[3 * it_ + 2]);
-  P[N + 1] = mk(ep.rx[3 * ir_], ep.rx[3 * ir_ + 1], ep.rx[3 * ir_ + 2]);
-  bool ok = true;
-  int kind[N];
+  v3<float> P[N + 2];
+  P[0] = mk(d2f_bits(ep.tx[3 * it_]), d2f_bits(ep.tx[3 * it_ + 1]), d2f_bits(ep.tx[3 * it_ + 2]));
+  P[N + 1] = mk(d2f_bits(ep.rx[3 * ir_]), d2f_bits(ep.rx[3 * ir_ + 1]), d2f_bits(ep.rx[3 * ir_ + 2]));
+  const float S32 = d2f_bits(S);
+  bool exact_bounds = false;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    kind[k] = sc.kind[cd.ids[k]];
-    const Rec<double> r = load_obj64(sc, cd.ids[k]);
-    P[k + 1] = point_at<double, false>(kind[k], r, Tc[2 * k], Tc[2 * k + 1]).X;
-    ok = ok && in_bounds64(kind[k], r, Tc[2 * k], Tc[2 * k + 1]);
+    const int kind = sc.kind[cd.ids[k]];
+    const Rec<float> r = load_obj32(sc, cd.ids[k]);
+    const float s = d2f_bits(Tc[2 * k]), t = d2f_bits(Tc[2 * k + 1]);
+    P[k + 1] = point_at<float, false>(kind, r, s, t).X;
+    const float bound = kind == K_PARAB ? r.v[13] : fmaxf(fabsf(r.v[3]), fabsf(r.v[7]));
+    exact_bounds = exact_bounds || !clearly_in32(kind, r, s, t, 1e-5f * S32 + 4e-7f * bound);
+  }
+  if (exact_bounds) {
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      if (!in_bounds64(sc.kind[cd.ids[k]], load_obj64(sc, cd.ids[k]), Tc[2 * k], Tc[2 * k + 1])) return false;
   }
   const double lmin = MIN_SEG_REL * S;
+  const float lclear = 10.0f * d2f_bits(lmin);
 #pragma unroll
   for (int j = 0; j <= N; ++j) {
-    const v3<double> d = P[j + 1] - P[j];
-    ok = ok && (sqrt(dot(d, d)) >= lmin);
+    const v3<float> d = P[j + 1] - P[j];
+    if (dot(d, d) >= lclear * lclear) continue;
+    const v3<double> e = point64<N>(sc, ep, cd, Tc, it_, ir_, j + 1) - point64<N>(sc, ep, cd, Tc, it_, ir_, j);
+    if (!(sqrt(dot(e, e)) >= lmin)) return false;
   }
-  if (!ok) return false;
   // visibility of every segment against every occluder
-  for (int j = 0; j <= N && ok; ++j) {
-    const v3<float> Af = cvt<float>(P[j]), Bf = cvt<float>(P[j + 1]);
+#pragma unroll
+  for (int j = 0; j <= N; ++j) {
+    const v3<float> Af = P[j], Bf = P[j + 1];
     // rectangles that hold an end of this segment cannot be crossed strictly
     const int own0 = j >= 1 ? sc.obj_occ[cd.ids[j - 1]] : -1;
     const int own1 = j < N ? sc.obj_occ[cd.ids[j]] : -1;
     for (int o = 0; o < sc.n_occ; ++o) {
       if (o == own0 || o == own1) continue;
       if (!box_overlap(occ_sm[4 * sc.n_occ + o], occ_sm[5 * sc.n_occ + o], Af, Bf)) continue;
-      int b;
-      if (sc.occ_kind[o] == 0) {
-        b = rect32(occ_sm, sc.n_occ, o, Af, Bf);
-        if (b < 0) b = blocks64(sc, o, P[j], P[j + 1]) ? 1 : 0;
-      } else {
-        b = blocks64(sc, o, P[j], P[j + 1]) ? 1 : 0;
-      }
-      if (b) { ok = false; break; }
+      int b = sc.occ_kind[o] == 0 ? rect32(occ_sm, sc.n_occ, o, Af, Bf) : -1;
+      if (b < 0)
+        b = blocks64(sc, o, point64<N>(sc, ep, cd, Tc, it_, ir_, j), point64<N>(sc, ep, cd, Tc, it_, ir_, j + 1))
+                ? 1
+                : 0;
+      if (b) return false;
     }
   }
-  return ok;
+  return true;
 }
 
-__global__ void __launch_bounds__(ACC_BLOCK) k_accept(DevScene sc, DevEnds ep, AccView av, double tau,
-                                                      ScratchView sv, int* err_flag) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ uint32_t warp_cnt[ACC_WARPS];
-  float4* occ_sm = reinterpret_cast<float4*>(smem_raw);
+// ------------------------------------------------------------ pipeline --
+constexpr int GROUP = 2048;                          // candidates per group
+constexpr int GROUP_WORDS = GROUP / 32;              // bitmap words per group
+constexpr int FLAG_PER_THREAD = GROUP / ACC_BLOCK;   // candidates per k_flag thread
+constexpr uint32_t LIST_SKIP = 0xFFFFFFFFu;          // list entry of a group that did not fit
+
+struct ValScratch {
+  unsigned long long* list_n;  // [1] list entries claimed
+  uint32_t* grp_count;         // [n_groups] valid paths per group
+  uint32_t* words;             // [n_groups * GROUP_WORDS] one bit per valid candidate
+  int64_t* grp_off;            // [n_groups] output position of the group's first path
+  uint8_t* ovf;                // [n_groups] 1 = the group's entries did not fit the list
+  uint32_t* list;              // [list_cap] candidates to test
+  int64_t list_cap;
+  int64_t n_groups;
+};
+
+constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+// Scratch bytes for n_groups groups and a list of list_cap entries.  The
+// first val_zero_bytes() of them (counter, counts, bitmap) are cleared by
+// every call; everything after is written before it is read.
+constexpr size_t val_zero_bytes(int64_t ng) {
+  return al256(8) + al256((size_t)ng * 4) + al256((size_t)ng * GROUP_WORDS * 4);
+}
+constexpr size_t val_bytes(int64_t ng, int64_t lc) {
+  return val_zero_bytes(ng) + al256((size_t)ng * 8) + al256((size_t)ng) + al256((size_t)lc * 4);
+}
+static ValScratch val_layout(unsigned char* base, int64_t ng, int64_t lc) {
+  ValScratch v;
+  size_t o = 0;
+  v.list_n = reinterpret_cast<unsigned long long*>(base + o);
+  o += al256(8);
+  v.grp_count = reinterpret_cast<uint32_t*>(base + o);
+  o += al256((size_t)ng * 4);
+  v.words = reinterpret_cast<uint32_t*>(base + o);
+  o += al256((size_t)ng * GROUP_WORDS * 4);
+  v.grp_off = reinterpret_cast<int64_t*>(base + o);
+  o += al256((size_t)ng * 8);
+  v.ovf = reinterpret_cast<uint8_t*>(base + o);
+  o += al256((size_t)ng);
+  v.list = reinterpret_cast<uint32_t*>(base + o);
+  v.list_cap = lc;
+  v.n_groups = ng;
+  return v;
+}
+
+__device__ __forceinline__ bool wanted(const AccView& av, int64_t c, double tau) {
+  return (av.status[c] & MPT_PATH_REFINED) && av.cost[c] < tau;
+}
+
+__device__ __forceinline__ void mark_valid(const ValScratch& vs, int64_t c) {
+  atomicOr(vs.words + (c >> 5), 1u << (c & 31));
+  atomicAdd(vs.grp_count + c / GROUP, 1u);
+}
+
+__device__ bool accept_candidate(const DevScene& sc, const DevEnds& ep, const AccView& av, int64_t c,
+                                 const float4* occ_sm) {
+  const Cand cd = decode(av.rec[c]);
+  if (!cand_in_range(sc, ep, cd)) return false;
+  double Tc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) Tc[i] = i < 2 * cd.order ? av.T[(int64_t)i * av.sol_cap + c] : 0.0;
+  switch (cd.order) {
+    case 1: return accept_one<1>(sc, ep, cd, Tc, occ_sm, sc.scale);
+    case 2: return accept_one<2>(sc, ep, cd, Tc, occ_sm, sc.scale);
+    case 3: return accept_one<3>(sc, ep, cd, Tc, occ_sm, sc.scale);
+    case 4: return accept_one<4>(sc, ep, cd, Tc, occ_sm, sc.scale);
+    default: return false;
+  }
+}
+
+// Stages the FP32 occluder records (fields 0-3) and their boxes (fields 4-5)
+// into shared memory with bulk copies; every thread waits, bounded, for them.
+// On a wait that gives up, the error flag is set, thread 0 waits (again
+// bounded) for the copy still in flight, and false is returned.
+__device__ bool stage_occluders(const DevScene& sc, float4* occ_sm, uint64_t* bar, int* err_flag) {
   const uint32_t field_bytes = (uint32_t)sc.n_occ * 16u;
   if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(bar, 1);
     fence_mbar_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0 && sc.n_occ > 0) {
-    // fields 0-3: FP32 occluder records; 4-5: their boxes (lo, hi)
-    mbar_expect_tx(&bar, 6u * field_bytes);
+  if (sc.n_occ == 0) return true;
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, 6u * field_bytes);
 #pragma unroll
-    for (int f = 0; f < 4; ++f) bulk_g2s(occ_sm + f * sc.n_occ, sc.c32 + f * sc.n_occ, field_bytes, &bar);
+    for (int f = 0; f < 4; ++f) bulk_g2s(occ_sm + f * sc.n_occ, sc.c32 + f * sc.n_occ, field_bytes, bar);
 #pragma unroll
-    for (int f = 0; f < 2; ++f)
-      bulk_g2s(occ_sm + (4 + f) * sc.n_occ, sc.cbox + f * sc.n_occ, field_bytes, &bar);
+    for (int f = 0; f < 2; ++f) bulk_g2s(occ_sm + (4 + f) * sc.n_occ, sc.cbox + f * sc.n_occ, field_bytes, bar);
   }
-  // bounded wait for the staged occluders
   bool staged = true;
-  if (sc.n_occ > 0) {
-    unsigned spins = 0;
-    while (!mbar_try_wait(&bar, 0)) {
-      if (++spins > MBAR_SPIN_LIMIT) { staged = false; break; }
+  unsigned spins = 0;
+  while (!mbar_try_wait(bar, 0)) {
+    if (++spins > MBAR_SPIN_LIMIT) {
+      staged = false;
+      break;
     }
   }
-  int64_t count = *av.count;
-  if (count > av.cap) count = av.cap;
-  const int64_t c = (int64_t)blockIdx.x * ACC_BLOCK + threadIdx.x;
-  bool valid = false;
-  if (staged && c < count) {
-    const uint8_t st = av.status[c];
-    const double cst = av.cost[c];
-    const Cand cd = decode(av.rec[c]);
-    if ((st & MPT_PATH_REFINED) && cst < tau && cand_in_range(sc, ep, cd)) {
-      double Tc[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) Tc[i] = i < 2 * cd.order ? av.T[(int64_t)i * av.sol_cap + c] : 0.0;
-      switch (cd.order) {
-        case 1: valid = accept_one<1>(sc, ep, cd, Tc, occ_sm, sc.scale); break;
-        case 2: valid = accept_one<2>(sc, ep, cd, Tc, occ_sm, sc.scale); break;
-        case 3: valid = accept_one<3>(sc, ep, cd, Tc, occ_sm, sc.scale); break;
-        case 4: valid = accept_one<4>(sc, ep, cd, Tc, occ_sm, sc.scale); break;
-        default: valid = false;
+  if (!staged) {
+    atomicExch(err_flag, MPT_ERR_TIMEOUT);
+    if (threadIdx.x == 0) {
+      unsigned s2 = 0;
+      while (!mbar_try_wait(bar, 0) && ++s2 < MBAR_SPIN_LIMIT) {
       }
     }
   }
-  if (!staged && threadIdx.x == 0) {
-    atomicExch(err_flag, MPT_ERR_TIMEOUT);
-    // a copy that may still be in flight must land before the block exits
-    unsigned spins = 0;
-    while (!mbar_try_wait(&bar, 0) && ++spins < MBAR_SPIN_LIMIT) {
-    }
+  return staged;
+}
+
+// One block per group: the group's wanted candidates go to the list in one
+// claim; a group whose entries do not all fit writes LIST_SKIP into the
+// claimed positions that exist and is marked for k_accept_ovf.
+__global__ void __launch_bounds__(ACC_BLOCK) k_flag(AccView av, double tau, ValScratch vs) {
+  __shared__ uint32_t warp_off[ACC_WARPS];
+  __shared__ unsigned long long s_base;
+  __shared__ int s_fit;
+  int64_t count = *av.count;
+  if (count > av.cap) count = av.cap;
+  const int64_t g = blockIdx.x;
+  const int64_t c0 = g * GROUP;
+  uint32_t mask = 0;
+#pragma unroll
+  for (int j = 0; j < FLAG_PER_THREAD; ++j) {
+    const int64_t c = c0 + (int64_t)j * ACC_BLOCK + threadIdx.x;
+    if (c < count && wanted(av, c, tau)) mask |= 1u << j;
   }
-  const uint32_t ball = __ballot_sync(0xffffffffu, valid);
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    sv.ballots[(int64_t)blockIdx.x * ACC_WARPS + wid] = ball;
-    warp_cnt[wid] = __popc(ball);
+  const uint32_t n = __popc(mask);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t x = n;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
   }
+  if (lane == 31) warp_off[wid] = x;
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t t = 0;
 #pragma unroll
-    for (int w = 0; w < ACC_WARPS; ++w) t += warp_cnt[w];
-    sv.blk_count[blockIdx.x] = t;
+    for (int w = 0; w < ACC_WARPS; ++w) {
+      const uint32_t v = warp_off[w];
+      warp_off[w] = t;
+      t += v;
+    }
+    unsigned long long base = 0;
+    int fit = 1;
+    if (t > 0) {
+      base = atomicAdd(vs.list_n, (unsigned long long)t);
+      fit = base + t <= (unsigned long long)vs.list_cap;
+    }
+    s_base = base;
+    s_fit = fit;
+    vs.ovf[g] = fit ? 0 : 1;
+  }
+  __syncthreads();
+  if (mask) {
+    unsigned long long pos = s_base + warp_off[wid] + (x - n);
+#pragma unroll
+    for (int j = 0; j < FLAG_PER_THREAD; ++j) {
+      if (!((mask >> j) & 1u)) continue;
+      if (s_fit) vs.list[pos] = (uint32_t)(c0 + (int64_t)j * ACC_BLOCK + threadIdx.x);
+      else if (pos < (unsigned long long)vs.list_cap) vs.list[pos] = LIST_SKIP;
+      ++pos;
+    }
   }
 }
 
-// Exclusive scan of n block counts by one CTA of 1024 threads.
+// Persistent grid over the list entries, one candidate per thread.
+__global__ void __launch_bounds__(ACC_BLOCK) k_accept_list(DevScene sc, DevEnds ep, AccView av, ValScratch vs,
+                                                           int* err_flag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  float4* occ_sm = reinterpret_cast<float4*>(smem_raw);
+  unsigned long long n = *vs.list_n;
+  if (n > (unsigned long long)vs.list_cap) n = (unsigned long long)vs.list_cap;
+  if ((unsigned long long)blockIdx.x * ACC_BLOCK >= n) return;  // the whole block
+  if (!stage_occluders(sc, occ_sm, &bar, err_flag)) return;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * ACC_BLOCK + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * ACC_BLOCK) {
+    const uint32_t c = vs.list[i];
+    if (c == LIST_SKIP || (int64_t)c >= av.cap) continue;
+    if (accept_candidate(sc, ep, av, c, occ_sm)) mark_valid(vs, c);
+  }
+}
+
+// Groups whose entries did not fit the list: every candidate of the group.
+__global__ void __launch_bounds__(ACC_BLOCK) k_accept_ovf(DevScene sc, DevEnds ep, AccView av, double tau,
+                                                          ValScratch vs, int* err_flag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  float4* occ_sm = reinterpret_cast<float4*>(smem_raw);
+  const int64_t g = blockIdx.x;
+  if (!vs.ovf[g]) return;  // the whole block
+  if (!stage_occluders(sc, occ_sm, &bar, err_flag)) return;
+  int64_t count = *av.count;
+  if (count > av.cap) count = av.cap;
+  for (int j = 0; j < FLAG_PER_THREAD; ++j) {
+    const int64_t c = g * GROUP + (int64_t)j * ACC_BLOCK + threadIdx.x;
+    if (c < count && wanted(av, c, tau) && accept_candidate(sc, ep, av, c, occ_sm)) mark_valid(vs, c);
+  }
+}
+
+// Exclusive scan of n counts by one CTA of 1024 threads; total to *total.
 __global__ void __launch_bounds__(1024) k_scan(const uint32_t* cnt, int64_t n, int64_t* off, int64_t* total) {
   __shared__ int64_t warp_tot[32];
   __shared__ int64_t s_base;
@@ -324,16 +492,9 @@ struct PathView {
   int64_t cap;
 };
 
-__global__ void __launch_bounds__(ACC_BLOCK) k_scatter(DevScene sc, DevEnds ep, AccView av, ScratchView sv,
-                                                       PathView pv) {
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t ball = sv.ballots[(int64_t)blockIdx.x * ACC_WARPS + wid];
-  if (!((ball >> lane) & 1u)) return;
-  int64_t pos = sv.blk_off[blockIdx.x];
-  for (int w = 0; w < wid; ++w) pos += __popc(sv.ballots[(int64_t)blockIdx.x * ACC_WARPS + w]);
-  pos += __popc(ball & ((1u << lane) - 1u));
-  if (pos >= pv.cap) return;
-  const int64_t c = (int64_t)blockIdx.x * ACC_BLOCK + threadIdx.x;
+// Writes valid candidate c as path number pos: parameters, points, length.
+__device__ void write_path(const DevScene& sc, const DevEnds& ep, const AccView& av, const PathView& pv, int64_t c,
+                           int64_t pos) {
   const Cand cd = decode(av.rec[c]);
   int it_, ir_;
   pair_ends(ep, cd.pair, it_, ir_);
@@ -359,21 +520,106 @@ __global__ void __launch_bounds__(ACC_BLOCK) k_scatter(DevScene sc, DevEnds ep, 
   const v3<double> B = mk(ep.rx[3 * ir_], ep.rx[3 * ir_ + 1], ep.rx[3 * ir_ + 2]);
   const v3<double> d = B - prev;
   len += sqrt(dot(d, d));
-  pv.cand[pos] = c;
   pv.length[pos] = len;
   pv.cost[pos] = av.cost[c];
 }
 
-static size_t scratch_bytes(int64_t n_blocks) {
-  return (size_t)n_blocks * ACC_WARPS * 4 + (size_t)n_blocks * 4 + (size_t)n_blocks * 8 + 256;
+// One warp per group; lane l owns bitmap words 2l and 2l+1 (candidates
+// 64l .. 64l+63 of the group), so a warp scan of the lanes' bit counts gives
+// every valid candidate its position in candidate order.  Only the candidate
+// index is written here; k_fill writes the rest, one thread per path.
+__global__ void __launch_bounds__(ACC_BLOCK) k_scatter(ValScratch vs, PathView pv) {
+  const int lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * ACC_WARPS + (threadIdx.x >> 5);
+  if (g >= vs.n_groups) return;  // the whole warp
+  const uint2 w = reinterpret_cast<const uint2*>(vs.words + g * GROUP_WORDS)[lane];
+  const uint32_t n = __popc(w.x) + __popc(w.y);
+  uint32_t x = n;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (n == 0) return;
+  int64_t pos = vs.grp_off[g] + (int64_t)(x - n);
+  const int64_t cbase = g * GROUP + (int64_t)lane * 64;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t bits = h ? w.y : w.x;
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1u;
+      if (pos < pv.cap) pv.cand[pos] = cbase + 32 * h + b;
+      ++pos;
+    }
+  }
 }
+
+// Persistent grid over the written paths: parameters, points, length, cost
+// of path i (consecutive threads write consecutive positions).
+__global__ void __launch_bounds__(ACC_BLOCK) k_fill(DevScene sc, DevEnds ep, AccView av, const int64_t* count,
+                                                    PathView pv) {
+  int64_t n = *count;
+  if (n > pv.cap) n = pv.cap;
+  for (int64_t i = (int64_t)blockIdx.x * ACC_BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * ACC_BLOCK)
+    write_path(sc, ep, av, pv, pv.cand[i], i);
+}
+
+// Enqueues the pipeline on scratch `base` (val_bytes(n_groups, list_cap)).
+static int run_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
+                        const mpt_solutions* sol, double tau, mpt_paths* out, int64_t* d_valid_count,
+                        unsigned char* base, int64_t n_groups, int64_t list_cap, bool may_overflow,
+                        cudaStream_t st) {
+  const ValScratch vs = val_layout(base, n_groups, list_cap);
+  MPT_CUDA_TRY(cudaMemsetAsync(base, 0, val_zero_bytes(n_groups), st));
+  AccView av{reinterpret_cast<const uint4*>(cand->rec), cand->count, cand->capacity, sol->T, sol->cost,
+             sol->status, sol->capacity};
+  const DevEnds ep = dev_ends(ends);
+  k_flag<<<(unsigned)n_groups, ACC_BLOCK, 0, st>>>(av, tau, vs);
+  MPT_LAUNCH_CHECK();
+  const size_t smem = (size_t)scene->d.n_occ * 96;
+  if (smem > 48 * 1024) {
+    cudaFuncSetAttribute(k_accept_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_accept_ovf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_accept_list, ACC_BLOCK, smem);
+  if (occ < 1) occ = 1;
+  int64_t grid = (int64_t)ctx->sms * occ;
+  const int64_t need = (list_cap + ACC_BLOCK - 1) / ACC_BLOCK;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  k_accept_list<<<(unsigned)grid, ACC_BLOCK, smem, st>>>(scene->d, ep, av, vs, ctx->err_flag);
+  MPT_LAUNCH_CHECK();
+  if (may_overflow) {
+    k_accept_ovf<<<(unsigned)n_groups, ACC_BLOCK, smem, st>>>(scene->d, ep, av, tau, vs, ctx->err_flag);
+    MPT_LAUNCH_CHECK();
+  }
+  k_scan<<<1, 1024, 0, st>>>(vs.grp_count, n_groups, vs.grp_off, d_valid_count);
+  MPT_LAUNCH_CHECK();
+  PathView pv{out->cand, out->X, out->T, out->length, out->cost, out->capacity};
+  k_scatter<<<(unsigned)((n_groups + ACC_WARPS - 1) / ACC_WARPS), ACC_BLOCK, 0, st>>>(vs, pv);
+  MPT_LAUNCH_CHECK();
+  if (out->capacity > 0) {
+    int64_t fgrid = (out->capacity + ACC_BLOCK - 1) / ACC_BLOCK;
+    if (fgrid > (int64_t)ctx->sms * 8) fgrid = (int64_t)ctx->sms * 8;
+    k_fill<<<(unsigned)fgrid, ACC_BLOCK, 0, st>>>(scene->d, ep, av, d_valid_count, pv);
+    MPT_LAUNCH_CHECK();
+  }
+  return MPT_OK;
+}
+
+// Candidate indices are stored in 32 bits (LIST_SKIP excluded).
+constexpr int64_t MAX_CANDIDATES = (int64_t)LIST_SKIP;
 
 int launch_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
                     const mpt_solutions* sol, double tau, mpt_paths* out, int64_t* d_valid_count, cudaStream_t st) {
   const int64_t cap = cand->capacity;
-  const int64_t n_blocks = (cap + ACC_BLOCK - 1) / ACC_BLOCK;
-  if (n_blocks < 1) return MPT_OK;
-  const size_t need = scratch_bytes(n_blocks);
+  if (cap > MAX_CANDIDATES) return MPT_ERR_CAPACITY;
+  const int64_t n_groups = (cap + GROUP - 1) / GROUP;
+  if (n_groups < 1) return MPT_OK;
+  // a list as long as the candidates: it never overflows
+  const size_t need = val_bytes(n_groups, cap);
   if (ctx->vscratch_bytes < need) {
     // grows the context's scratch (stream-ordered free of the old buffer)
     if (ctx->vscratch) MPT_CUDA_TRY(cudaFreeAsync(ctx->vscratch, st));
@@ -382,40 +628,22 @@ int launch_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* e
     MPT_CUDA_TRY(cudaMallocAsync(&ctx->vscratch, need, st));
     ctx->vscratch_bytes = need;
   }
-  unsigned char* base = reinterpret_cast<unsigned char*>(ctx->vscratch);
-  ScratchView sv;
-  sv.blk_off = reinterpret_cast<int64_t*>(base);
-  sv.blk_count = reinterpret_cast<uint32_t*>(base + (size_t)n_blocks * 8);
-  sv.ballots = reinterpret_cast<uint32_t*>(base + (size_t)n_blocks * 12);
-  AccView av{reinterpret_cast<const uint4*>(cand->rec), cand->count, cap, sol->T, sol->cost, sol->status,
-             sol->capacity};
-  const DevEnds ep = dev_ends(ends);
-  const size_t smem = (size_t)scene->d.n_occ * 96;
-  if (smem > 48 * 1024) {
-    cudaFuncSetAttribute(k_accept, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  }
-  k_accept<<<(unsigned)n_blocks, ACC_BLOCK, smem, st>>>(scene->d, ep, av, tau, sv, ctx->err_flag);
-  MPT_LAUNCH_CHECK();
-  k_scan<<<1, 1024, 0, st>>>(sv.blk_count, n_blocks, sv.blk_off, d_valid_count);
-  MPT_LAUNCH_CHECK();
-  PathView pv{out->cand, out->X, out->T, out->length, out->cost, out->capacity};
-  k_scatter<<<(unsigned)n_blocks, ACC_BLOCK, 0, st>>>(scene->d, ep, av, sv, pv);
-  MPT_LAUNCH_CHECK();
-  return MPT_OK;
+  return run_validate(ctx, scene, ends, cand, sol, tau, out, d_valid_count,
+                      reinterpret_cast<unsigned char*>(ctx->vscratch), n_groups, cap, false, st);
 }
 
 // --------------------------------------------- validation without allocation --
 // Scratch of mpt_validate_noalloc: one fixed array in the library's device
 // data, present on every GPU that loads the library until the process exits.
-// It serves up to NOALLOC_MAX_CANDIDATES candidates (2^24): per block of 256
-// candidates one 8-byte offset, one 4-byte count and eight 4-byte ballots,
-// 2.9 MB in all.  Every word a call reads is written earlier in the same call
-// (k_accept writes the count and ballots of every block it covers, k_scan
-// every offset), so nothing needs clearing between calls; calls that overlap
-// on the GPU (two streams, two host threads) race on the array.
+// It serves up to NOALLOC_MAX_CANDIDATES candidates (2^24) with a list of
+// NOALLOC_LIST entries (2^18); groups whose entries do not fit are tested in
+// full by k_accept_ovf.  3.3 MB in all.  The call clears the counter, counts
+// and bitmap and writes every other word before reading it; calls that
+// overlap on the GPU (two streams, two host threads) race on the array.
 constexpr int64_t NOALLOC_MAX_CANDIDATES = int64_t(1) << 24;
-constexpr int64_t NOALLOC_MAX_BLOCKS = NOALLOC_MAX_CANDIDATES / ACC_BLOCK;
-constexpr size_t NOALLOC_BYTES = (size_t)NOALLOC_MAX_BLOCKS * (8 + 4 + 4 * ACC_WARPS);
+constexpr int64_t NOALLOC_GROUPS = NOALLOC_MAX_CANDIDATES / GROUP;
+constexpr int64_t NOALLOC_LIST = int64_t(1) << 18;
+constexpr size_t NOALLOC_BYTES = val_bytes(NOALLOC_GROUPS, NOALLOC_LIST);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 // Device address of g_noalloc_scratch on `device`, looked up once per device
@@ -448,30 +676,13 @@ static int launch_validate_noalloc(mpt_ctx* ctx, const mpt_scene* scene, const m
                                    mpt_paths* out, int64_t* d_valid_count, cudaStream_t st) {
   const int64_t cap = cand->capacity;
   if (cap > NOALLOC_MAX_CANDIDATES) return MPT_ERR_CAPACITY;
-  const int64_t n_blocks = (cap + ACC_BLOCK - 1) / ACC_BLOCK;
-  if (n_blocks < 1) return MPT_OK;
+  const int64_t n_groups = (cap + GROUP - 1) / GROUP;
+  if (n_groups < 1) return MPT_OK;
   unsigned char* base = nullptr;
   const int rc = noalloc_scratch(ctx->device, &base);
   if (rc != MPT_OK) return rc;
-  ScratchView sv;
-  sv.blk_off = reinterpret_cast<int64_t*>(base);
-  sv.blk_count = reinterpret_cast<uint32_t*>(base + (size_t)NOALLOC_MAX_BLOCKS * 8);
-  sv.ballots = reinterpret_cast<uint32_t*>(base + (size_t)NOALLOC_MAX_BLOCKS * 12);
-  AccView av{reinterpret_cast<const uint4*>(cand->rec), cand->count, cap, sol->T, sol->cost, sol->status,
-             sol->capacity};
-  const DevEnds ep = dev_ends(ends);
-  const size_t smem = (size_t)scene->d.n_occ * 96;
-  if (smem > 48 * 1024) {
-    cudaFuncSetAttribute(k_accept, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  }
-  k_accept<<<(unsigned)n_blocks, ACC_BLOCK, smem, st>>>(scene->d, ep, av, tau, sv, ctx->err_flag);
-  MPT_LAUNCH_CHECK();
-  k_scan<<<1, 1024, 0, st>>>(sv.blk_count, n_blocks, sv.blk_off, d_valid_count);
-  MPT_LAUNCH_CHECK();
-  PathView pv{out->cand, out->X, out->T, out->length, out->cost, out->capacity};
-  k_scatter<<<(unsigned)n_blocks, ACC_BLOCK, 0, st>>>(scene->d, ep, av, sv, pv);
-  MPT_LAUNCH_CHECK();
-  return MPT_OK;
+  return run_validate(ctx, scene, ends, cand, sol, tau, out, d_valid_count, base, n_groups, NOALLOC_LIST, true,
+                      st);
 }
 
 }  // namespace mpt

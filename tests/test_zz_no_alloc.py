@@ -76,3 +76,27 @@ def test_noalloc_rejects_more_candidates_than_its_array_serves(mpt):
     rc = _call_noalloc(mpt, ds, cands, sols, paths, torch.cuda.current_stream())
     assert rc == mpt.MPT_ERR_CAPACITY
     assert "CAPACITY" in mpt.status_string(rc)
+
+
+def test_noalloc_groups_beyond_its_list_match_validate(mpt):
+    # FP64-plain solutions mark every candidate as final, so the converged
+    # ones (about 400k of 602k here) exceed the fixed list of 2^18 entries:
+    # the groups that do not fit are tested in full by the overflow kernel
+    ctx = mpt.Context(0)
+    stream = torch.cuda.current_stream()
+    sc = S.urban_block(8)
+    ds = mpt.DeviceScene(ctx, sc)
+    cands = mpt.enumerate_candidates(ds, 2, S.CONFIG_SPECS["urban_block"])
+    sols = mpt.solve(ds, cands, mpt.FP64_PLAIN)
+    listed = int(((sols.status.to(torch.int32) & mpt.PATH_REFINED) != 0).logical_and(sols.cost < mpt.TAU).sum())
+    assert listed > (1 << 18)
+    want = mpt.validate(ds, cands, sols, capacity=cands.capacity)
+    got = mpt.alloc_paths(cands.capacity, ds.tx.device)
+    assert _call_noalloc(mpt, ds, cands, sols, got, stream) == mpt.MPT_OK
+    torch.cuda.synchronize()
+    n = want.n()
+    assert n > 0 and got.n() == n
+    assert torch.equal(got.cand[:n], want.cand[:n])
+    assert torch.equal(got.X[:, :n], want.X[:, :n])
+    assert torch.equal(got.length[:n], want.length[:n])
+    assert ctx.check() == mpt.MPT_OK
