@@ -240,9 +240,9 @@ def run_ours(args):
         n_valid = paths.n()
         flops = algorithmic_flops(mpt, sc, cands, sols, n_cand)
         # enumerate (2) + solve (endpoint copy, 4 orders x {solver, visibility
-        # prescreen, refinement}) + validate (list, test, scan, scatter, fill) +
+        # prescreen, refinement, refinement fallback}) + validate (list, test, scan, scatter, fill) +
         # adjoint (one launch per order)
-        launches_per_step = 2 + (1 + 4 * 3) + 5 + 4
+        launches_per_step = 2 + (1 + 4 * 4) + 5 + 4
 
         # ---- device-resident timing
         ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -357,7 +357,7 @@ def run_ours(args):
                      "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {SM_MAX_MHZ_NOMINAL:.0f} MHz (derived)",
                      "solve_ms": solve_avg_ms, "fp32_flops_per_launch": flops,
-                     "traffic": profile_traffic("mpt_solve")},
+                     "traffic": profile_traffic("mpt_solve") if args.rx_side == 32 else None},
         "fp64_plain": {"ms_per_step": float(np.median(fp64_ms)),
                        "value": n_cand * ws / (float(np.median(fp64_ms)) * 1e-3), "unit": UNIT,
                        "valid_paths_per_step": n_valid_fp64},

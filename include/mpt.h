@@ -78,8 +78,10 @@ enum { MPT_OCC_RECT = 0, MPT_OCC_PARABOLOID = 1 };
 enum {
   MPT_FP64_PLAIN = 0,       /* FP64 throughout (the plain GPU method) */
   MPT_FP32 = 1,             /* FP32 iterations only, no refinement */
-  MPT_FP32_FP64REFINE = 2   /* FP32 iterations, FP64 refinement of candidates
-                               that pass the FP32 cost/bounds prescreen */
+  MPT_FP32_FP64REFINE = 2   /* FP32 iterations, then refinement of candidates
+                               that pass the FP32 cost/bounds/visibility
+                               prescreen in float-float arithmetic (48-bit
+                               significand), stored as FP64 */
 };
 
 /* Per-candidate termination status (low 4 bits) and flags. */
@@ -89,8 +91,10 @@ enum {
   MPT_PATH_DIVERGED = 2,    /* a point left the cube of half-side 1e3 S */
   MPT_PATH_STALLED = 3,     /* line search could not decrease the cost */
   MPT_PATH_NONFINITE = 4,   /* NaN / Inf in the cost */
-  MPT_PATH_REFINED = 0x10,  /* flag: FP64 refinement ran; cost is FP64 */
-  MPT_PATH_PRESCREENED = 0x20 /* flag: FP32 prescreen rejected (no refinement) */
+  MPT_PATH_REFINED = 0x10,  /* flag: final stage ran (FP64 solve or refinement) */
+  MPT_PATH_PRESCREENED = 0x20, /* flag: FP32 prescreen rejected (no refinement) */
+  MPT_PATH_FALLBACK = 0x40  /* flag: refinement needed full Gauss-Newton in
+                               float-float (ill-conditioned path) */
 };
 
 typedef struct mpt_ctx mpt_ctx;

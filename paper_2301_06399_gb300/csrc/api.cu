@@ -226,6 +226,7 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
       cbox[(size_t)4 * q + j] = (float)(lo[j] - 0.01);
       cbox[(size_t)4 * (nc + q) + j] = (float)(hi[j] + 0.01);
     }
+    cbox[(size_t)4 * q + 3] = desc->occ_kind[q] == MPT_OCC_RECT ? 0.f : 1.f;  // lo.w: kind
   }
   const size_t s_kind = align256((size_t)no * 4), s_o32 = align256((size_t)no * 64),
                s_o64 = align256((size_t)no * 128), s_ck = align256((size_t)nc * 4 + 4),

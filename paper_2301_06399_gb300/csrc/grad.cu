@@ -6,36 +6,39 @@
 //   dtheta += gL dL/dtheta|explicit + gX dX/dtheta|explicit - z^T drho/dtheta.
 // theta: TX (a fixed point before interaction 1), RX (after interaction n)
 // and the offset d of each plane <n, X> = d (its points move along n).
-// One thread per valid path, FP64 throughout (a few thousand paths).
+// One thread per valid path, in float-float (about 48 significand bits).
 #include "mpt_internal.cuh"
 
 namespace mpt {
 
 constexpr int GRAD_BLOCK = 128;
 
+// Working precision of the adjoint: float-float (see ff.cuh).
+using S = ff;
+
 // Law residual of one interaction and the linear maps that give its rows
 // for a displacement w of the previous point, this point and the next point.
 struct Inter {
   bool refl;
-  v3<double> ih, rh, nh, eh;
-  double ia, ib;
+  v3<S> ih, rh, nh, eh;
+  S ia, ib;
   // reflection: H P_i w / a (prev), -(P_r w / b + H P_i w / a) (this), P_r w / b (next)
   // diffraction: -<e, P_i w>/a (prev), <e,P_i w>/a + <e,P_r w>/b (this), -<e, P_r w>/b (next)
-  __device__ v3<double> Pi(const v3<double>& w) const { return axpy(-dot(ih, w), ih, w) * ia; }
-  __device__ v3<double> Pr(const v3<double>& w) const { return axpy(-dot(rh, w), rh, w) * ib; }
-  __device__ v3<double> H(const v3<double>& w) const { return axpy(-2.0 * dot(nh, w), nh, w); }
+  __device__ v3<S> Pi(const v3<S>& w) const { return axpy(-dot(ih, w), ih, w) * ia; }
+  __device__ v3<S> Pr(const v3<S>& w) const { return axpy(-dot(rh, w), rh, w) * ib; }
+  __device__ v3<S> H(const v3<S>& w) const { return axpy(S(-2) * dot(nh, w), nh, w); }
   // rows (3 for reflection; component x only for diffraction)
-  __device__ v3<double> prev(const v3<double>& w) const {
+  __device__ v3<S> prev(const v3<S>& w) const {
     if (refl) return H(Pi(w));
-    return mk(-dot(eh, Pi(w)), 0.0, 0.0);
+    return mk(-dot(eh, Pi(w)), S(0), S(0));
   }
-  __device__ v3<double> self(const v3<double>& w) const {
+  __device__ v3<S> self(const v3<S>& w) const {
     if (refl) return -(Pr(w) + H(Pi(w)));
-    return mk(dot(eh, Pi(w)) + dot(eh, Pr(w)), 0.0, 0.0);
+    return mk(dot(eh, Pi(w)) + dot(eh, Pr(w)), S(0), S(0));
   }
-  __device__ v3<double> next(const v3<double>& w) const {
+  __device__ v3<S> next(const v3<S>& w) const {
     if (refl) return Pr(w);
-    return mk(-dot(eh, Pr(w)), 0.0, 0.0);
+    return mk(-dot(eh, Pr(w)), S(0), S(0));
   }
 };
 
@@ -53,43 +56,44 @@ __device__ bool grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, 
   constexpr int Q = 2 * N;
   int it_, ir_;
   pair_ends(ep, cd.pair, it_, ir_);
-  const v3<double> A = mk(ep.tx[3 * it_], ep.tx[3 * it_ + 1], ep.tx[3 * it_ + 2]);
-  const v3<double> B = mk(ep.rx[3 * ir_], ep.rx[3 * ir_ + 1], ep.rx[3 * ir_ + 2]);
+  const v3<S> A = load_end_ff(ep.tx, it_);
+  const v3<S> B = load_end_ff(ep.rx, ir_);
+  const S gLs = ff_from_double(gL);
   int kind[N];
-  Rec<double> rec[N];
-  double prm[Q];
+  Rec<S> rec[N];
+  S prm[Q];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     kind[k] = sc.kind[cd.ids[k]];
-    rec[k] = load_obj64(sc, cd.ids[k]);
-    prm[2 * k] = Tc[2 * k];
-    prm[2 * k + 1] = Tc[2 * k + 1];
+    rec[k] = load_obj_ff(sc, cd.ids[k]);
+    prm[2 * k] = ff_from_double(Tc[2 * k]);
+    prm[2 * k + 1] = ff_from_double(Tc[2 * k + 1]);
   }
   // normal matrix at the solution
-  double jtj[Q * (Q + 1) / 2], g[Q];
+  S jtj[Q * (Q + 1) / 2], g[Q];
   bool ok;
-  eval_path<N, double, double, true>(kind, rec, prm, A, B, jtj, g, ok);
+  eval_path<N, S, S, true>(kind, rec, prm, A, B, jtj, g, ok);
 #pragma unroll
   for (int k = 0; k < N; ++k)
-    if (is_edge(kind[k])) jtj[tri(2 * k + 1, 2 * k + 1)] = 1.0;
-  if (!cholesky<Q, double>(jtj, 0.0)) return false;
+    if (is_edge(kind[k])) jtj[tri(2 * k + 1, 2 * k + 1)] = S(1);
+  if (!cholesky<Q, S>(jtj, S(0))) return false;
   // geometry
-  PointT<double> pt[N];
+  PointT<S> pt[N];
 #pragma unroll
-  for (int k = 0; k < N; ++k) pt[k] = point_at<double, true>(kind[k], rec[k], prm[2 * k], prm[2 * k + 1]);
-  v3<double> u[N + 1];
-  double il[N + 1];
+  for (int k = 0; k < N; ++k) pt[k] = point_at<S, true>(kind[k], rec[k], prm[2 * k], prm[2 * k + 1]);
+  v3<S> u[N + 1];
+  S il[N + 1];
 #pragma unroll
   for (int j = 0; j <= N; ++j) {
-    const v3<double> a = j == 0 ? A : pt[j - 1].X;
-    const v3<double> b = j == N ? B : pt[j].X;
-    const v3<double> d = b - a;
+    const v3<S> a = j == 0 ? A : pt[j - 1].X;
+    const v3<S> b = j == N ? B : pt[j].X;
+    const v3<S> d = b - a;
     il[j] = rsq(dot(d, d));
     u[j] = d * il[j];
   }
   Inter in[N];
-  double curv_c[N];
-  double inv_nn[N];
+  S curv_c[N];
+  S inv_nn[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     in[k].refl = !is_edge(kind[k]);
@@ -97,56 +101,56 @@ __device__ bool grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, 
     in[k].rh = u[k + 1];
     in[k].ia = il[k];
     in[k].ib = il[k + 1];
-    inv_nn[k] = 0.0;
+    inv_nn[k] = S(0);
     if (kind[k] == K_PLANE) {
       in[k].nh = rec[k].f3(12);
     } else if (kind[k] == K_PARAB) {
-      const double q2 = rec[k].v[14];
-      const v3<double> nraw = axpy(-prm[2 * k + 1] * q2, rec[k].f3(4), axpy(-prm[2 * k] * q2, rec[k].f3(0), rec[k].f3(8)));
+      const S q2 = rec[k].v[14];
+      const v3<S> nraw = axpy(-prm[2 * k + 1] * q2, rec[k].f3(4), axpy(-prm[2 * k] * q2, rec[k].f3(0), rec[k].f3(8)));
       inv_nn[k] = rsq(dot(nraw, nraw));
       in[k].nh = nraw * inv_nn[k];
     } else if (kind[k] == K_LINE) {
       in[k].eh = rec[k].f3(4);
     } else {
-      double sn, cs;
+      S sn, cs;
       sincos_(prm[2 * k], sn, cs);
       in[k].eh = axpy(cs, rec[k].f3(8), rec[k].f3(4) * (-sn));
     }
-    curv_c[k] = in[k].refl ? dot(in[k].ih, in[k].nh) : 0.0;
+    curv_c[k] = in[k].refl ? dot(in[k].ih, in[k].nh) : S(0);
   }
   // v = gL dL/dT + gX dX/dT ; dL/dX_k = u[k] - u[k+1]
-  double v[Q];
+  S v[Q];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    v3<double> gx = (u[k] - u[k + 1]) * gL;
-    if (gX) gx = gx + mk(gX[3 * k], gX[3 * k + 1], gX[3 * k + 2]);
+    v3<S> gx = (u[k] - u[k + 1]) * gLs;
+    if (gX) gx = gx + mk(ff_from_double(gX[3 * k]), ff_from_double(gX[3 * k + 1]), ff_from_double(gX[3 * k + 2]));
     v[2 * k] = -dot(gx, pt[k].w0);
-    v[2 * k + 1] = is_edge(kind[k]) ? 0.0 : -dot(gx, pt[k].w1);
+    v[2 * k + 1] = is_edge(kind[k]) ? S(0) : -dot(gx, pt[k].w1);
   }
-  double lam[Q];
-  chol_solve<Q, double>(jtj, v, lam);  // solves (J^T J) lam = -v' = gL dL/dT + gX dX/dT
+  S lam[Q];
+  chol_solve<Q, S>(jtj, v, lam);  // solves (J^T J) lam = -v' = gL dL/dT + gX dX/dT
   // z_k = J_k lambda: point displacements D_k = lam_2k w0 + lam_2k+1 w1
-  v3<double> D[N];
+  v3<S> D[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) D[k] = axpy(lam[2 * k + 1], pt[k].w1, pt[k].w0 * lam[2 * k]);
-  v3<double> z[N];
+  v3<S> z[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    v3<double> r = in[k].self(D[k]);
+    v3<S> r = in[k].self(D[k]);
     if (k >= 1) r = r + in[k].prev(D[k - 1]);
     if (k + 1 < N) r = r + in[k].next(D[k + 1]);
     if (kind[k] == K_PARAB) {
       // normal variation: 2 (<i, dn> n + <i, n> dn), dn from the parameters
-      const double q2 = rec[k].v[14];
-      const v3<double> craw = axpy(lam[2 * k + 1], rec[k].f3(4), rec[k].f3(0) * lam[2 * k]) * (-q2);
-      const v3<double> dn = axpy(-dot(in[k].nh, craw), in[k].nh, craw) * inv_nn[k];
-      r = axpy(2.0 * dot(in[k].ih, dn), in[k].nh, r);
-      r = axpy(2.0 * curv_c[k], dn, r);
+      const S q2 = rec[k].v[14];
+      const v3<S> craw = axpy(lam[2 * k + 1], rec[k].f3(4), rec[k].f3(0) * lam[2 * k]) * (-q2);
+      const v3<S> dn = axpy(-dot(in[k].nh, craw), in[k].nh, craw) * inv_nn[k];
+      r = axpy(S(2) * dot(in[k].ih, dn), in[k].nh, r);
+      r = axpy(S(2) * curv_c[k], dn, r);
     } else if (kind[k] == K_ARC) {
-      double sn, cs;
+      S sn, cs;
       sincos_(prm[2 * k], sn, cs);
-      const v3<double> de = axpy(-sn, rec[k].f3(8), rec[k].f3(4) * (-cs));
-      r.x += dot(in[k].ih - in[k].rh, de) * lam[2 * k];
+      const v3<S> de = axpy(-sn, rec[k].f3(8), rec[k].f3(4) * (-cs));
+      r.x = r.x + dot(in[k].ih - in[k].rh, de) * lam[2 * k];
     }
     z[k] = r;
   }
@@ -154,29 +158,29 @@ __device__ bool grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, 
   o.ir = ir_;
   // TX: a displacement of X_0 enters interaction 0 as "previous point"
   if (want_tx) {
-    const v3<double> ex = mk(1.0, 0.0, 0.0), ey = mk(0.0, 1.0, 0.0), ez = mk(0.0, 0.0, 1.0);
-    o.tx[0] = -gL * u[0].x - dot(z[0], in[0].prev(ex));
-    o.tx[1] = -gL * u[0].y - dot(z[0], in[0].prev(ey));
-    o.tx[2] = -gL * u[0].z - dot(z[0], in[0].prev(ez));
+    const v3<S> ex = mk(S(1), S(0), S(0)), ey = mk(S(0), S(1), S(0)), ez = mk(S(0), S(0), S(1));
+    o.tx[0] = to_double(-gLs * u[0].x - dot(z[0], in[0].prev(ex)));
+    o.tx[1] = to_double(-gLs * u[0].y - dot(z[0], in[0].prev(ey)));
+    o.tx[2] = to_double(-gLs * u[0].z - dot(z[0], in[0].prev(ez)));
   }
   if (want_rx) {
-    const v3<double> ex = mk(1.0, 0.0, 0.0), ey = mk(0.0, 1.0, 0.0), ez = mk(0.0, 0.0, 1.0);
-    o.rx[0] = gL * u[N].x - dot(z[N - 1], in[N - 1].next(ex));
-    o.rx[1] = gL * u[N].y - dot(z[N - 1], in[N - 1].next(ey));
-    o.rx[2] = gL * u[N].z - dot(z[N - 1], in[N - 1].next(ez));
+    const v3<S> ex = mk(S(1), S(0), S(0)), ey = mk(S(0), S(1), S(0)), ez = mk(S(0), S(0), S(1));
+    o.rx[0] = to_double(gLs * u[N].x - dot(z[N - 1], in[N - 1].next(ex)));
+    o.rx[1] = to_double(gLs * u[N].y - dot(z[N - 1], in[N - 1].next(ey)));
+    o.rx[2] = to_double(gLs * u[N].z - dot(z[N - 1], in[N - 1].next(ez)));
   }
   if (want_obj) {
 #pragma unroll
     for (int m = 0; m < N; ++m) {
       o.obj[m] = 0.0;
       if (kind[m] != K_PLANE) continue;
-      const v3<double> n = rec[m].f3(12);
-      double gd = gL * dot(u[m] - u[m + 1], n);
-      if (gX) gd += dot(mk(gX[3 * m], gX[3 * m + 1], gX[3 * m + 2]), n);
-      gd -= dot(z[m], in[m].self(n));
-      if (m >= 1) gd -= dot(z[m - 1], in[m - 1].next(n));
-      if (m + 1 < N) gd -= dot(z[m + 1], in[m + 1].prev(n));
-      o.obj[m] = gd;
+      const v3<S> n = rec[m].f3(12);
+      S gd = gLs * dot(u[m] - u[m + 1], n);
+      if (gX) gd = gd + dot(mk(ff_from_double(gX[3 * m]), ff_from_double(gX[3 * m + 1]), ff_from_double(gX[3 * m + 2])), n);
+      gd = gd - dot(z[m], in[m].self(n));
+      if (m >= 1) gd = gd - dot(z[m - 1], in[m - 1].next(n));
+      if (m + 1 < N) gd = gd - dot(z[m + 1], in[m + 1].prev(n));
+      o.obj[m] = to_double(gd);
     }
   }
   return true;
@@ -223,8 +227,8 @@ struct GradView {
 // loop bounds are uniform over the block so that whole warps reach the
 // aggregated atomics together.
 template <int N>
-__global__ void __launch_bounds__(GRAD_BLOCK) k_grad(DevScene sc, DevEnds ep, GradView gv, double* g_tx,
-                                                     double* g_rx, double* g_obj) {
+__global__ void __launch_bounds__(GRAD_BLOCK, (N <= 2 ? 3 : 1)) k_grad(DevScene sc, DevEnds ep, GradView gv,
+                                                                       double* g_tx, double* g_rx, double* g_obj) {
   int64_t n = *gv.count;
   if (n > gv.pcap) n = gv.pcap;
   for (int64_t i0 = (int64_t)blockIdx.x * GRAD_BLOCK; i0 < n; i0 += (int64_t)gridDim.x * GRAD_BLOCK) {

@@ -7,6 +7,7 @@
 #include <cstdio>
 
 #include "../../include/mpt.h"
+#include "ff.cuh"
 #include "mpt_math.cuh"
 
 namespace mpt {
@@ -24,7 +25,7 @@ struct DevScene {
   const float4* c32;        // [4][n_occ]
   const double2* c64;       // [8][n_occ]
   const int32_t* obj_occ;   // [n_obj]: occluder holding this plane's rectangle, or -1
-  const float4* cbox;       // [2][n_occ]: occluder bounding boxes (lo, hi), grown by 1 cm
+  const float4* cbox;       // [2][n_occ]: occluder boxes (lo, hi) grown by 1 cm; lo.w = 0 rectangle, 1 paraboloid
   double scale;
 };
 
@@ -40,12 +41,21 @@ struct DevEnds {
   const double* tx;
   const double* rx;
   int n_tx, n_rx, pair_mode;
+  // p / n_rx by multiplication: q = (t + ((p - t) >> s1)) >> s2 with
+  // t = umulhi(m, p) (Granlund and Montgomery, "Division by invariant
+  // integers using multiplication", 1994), exact for every 32-bit p.  A
+  // hardware-less integer division would take float conversions, which run
+  // on GB300's slow FP64 pipe.
+  uint32_t rx_m;
+  int rx_s1, rx_s2;
 };
 
 __device__ __forceinline__ void pair_ends(const DevEnds& e, uint32_t p, int& it, int& ir) {
   if (e.pair_mode == 0) {
-    it = (int)(p / (uint32_t)e.n_rx);
-    ir = (int)(p % (uint32_t)e.n_rx);
+    const uint32_t t = __umulhi(e.rx_m, p);
+    const uint32_t q = (t + ((p - t) >> e.rx_s1)) >> e.rx_s2;
+    it = (int)q;
+    ir = (int)(p - q * (uint32_t)e.n_rx);
   } else {
     it = ir = (int)p;
   }
@@ -68,6 +78,22 @@ __device__ __forceinline__ Rec<double> load_obj64(const DevScene& s, int o) {
     r.v[2 * f] = q.x; r.v[2 * f + 1] = q.y;
   }
   return r;
+}
+
+// Scene values in float-float (the refinement's working precision).
+__device__ __forceinline__ Rec<ff> load_obj_ff(const DevScene& s, int o) {
+  Rec<ff> r;
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    const double2 q = __ldg(&s.o64[f * s.n_obj + o]);
+    r.v[2 * f] = ff_from_double(q.x);
+    r.v[2 * f + 1] = ff_from_double(q.y);
+  }
+  return r;
+}
+__device__ __forceinline__ v3<ff> load_end_ff(const double* p, int i) {
+  return mk(ff_from_double(__ldg(p + 3 * i)), ff_from_double(__ldg(p + 3 * i + 1)),
+            ff_from_double(__ldg(p + 3 * i + 2)));
 }
 
 // SplitMix64 output function (Steele, Lea, Flood 2014): mixes x + gamma.
@@ -163,6 +189,14 @@ inline DevEnds dev_ends(const mpt_endpoints* e) {
   d.n_tx = e->n_tx;
   d.n_rx = e->n_rx;
   d.pair_mode = e->pair_mode;
+  // multiplier for division by n_rx (>= 1): l = ceil(log2 n_rx),
+  // m = floor(2^32 (2^l - n_rx) / n_rx) + 1
+  const uint32_t dv = e->n_rx > 0 ? (uint32_t)e->n_rx : 1u;
+  int l = 0;
+  while ((1ull << l) < dv) ++l;
+  d.rx_m = (uint32_t)(((1ull << 32) * ((1ull << l) - dv)) / dv + 1);
+  d.rx_s1 = l < 1 ? l : 1;
+  d.rx_s2 = l - 1 > 0 ? l - 1 : 0;
   return d;
 }
 inline int64_t n_pairs(const mpt_endpoints* e) {

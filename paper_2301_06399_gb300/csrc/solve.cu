@@ -25,6 +25,7 @@
 // kernel A only.
 #include <type_traits>
 
+#include "ff.cuh"
 #include "mpt_internal.cuh"
 
 namespace mpt {
@@ -455,33 +456,40 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_mixed(DevScene sc, DevEnds e
 constexpr float CLEAR_M = 0.25f;
 constexpr float PRESCREEN_VIS_COST = 1e-10f;
 
-__device__ __forceinline__ bool clearly_blocked(const DevScene& sc, const v3<float>& A, const v3<float>& B) {
-  for (int o = 0; o < sc.n_occ; ++o) {
-    if (__ldg(sc.occ_kind + o) != 0) continue;
-    if (!box_overlap(__ldg(sc.cbox + o), __ldg(sc.cbox + sc.n_occ + o), A, B)) continue;
-    const float4 f0 = __ldg(sc.c32 + o), f1 = __ldg(sc.c32 + sc.n_occ + o), f2 = __ldg(sc.c32 + 2 * sc.n_occ + o),
-                 f3 = __ldg(sc.c32 + 3 * sc.n_occ + o);
-    const v3<float> O = mk(f0.x, f0.y, f0.z), n = mk(f3.x, f3.y, f3.z);
-    const float sA = dot(A - O, n), sB = dot(B - O, n);
-    if (!((sA > CLEAR_M && sB < -CLEAR_M) || (sA < -CLEAR_M && sB > CLEAR_M))) continue;
-    const float t = sA / (sA - sB);
-    const v3<float> P = axpy(t, B - A, A) - O;
-    const float uu = dot(P, mk(f1.x, f1.y, f1.z)), vv = dot(P, mk(f2.x, f2.y, f2.z));
-    if (uu > CLEAR_M && uu < f0.w - CLEAR_M && vv > CLEAR_M && vv < f1.w - CLEAR_M) return true;
-  }
-  return false;
+// Occluder o (staged in shared memory: fields 0-3 of the FP32 records, then
+// the boxes lo (w = kind) and hi) crosses segment AB with a clearance of
+// CLEAR_M everywhere.
+__device__ __forceinline__ bool clearly_crosses(const float4* sm, int n_occ, int o, const v3<float>& A,
+                                                const v3<float>& B) {
+  const float4 f0 = sm[o], f1 = sm[n_occ + o], f2 = sm[2 * n_occ + o], f3 = sm[3 * n_occ + o];
+  const v3<float> O = mk(f0.x, f0.y, f0.z), n = mk(f3.x, f3.y, f3.z);
+  const float sA = dot(A - O, n), sB = dot(B - O, n);
+  if (!((sA > CLEAR_M && sB < -CLEAR_M) || (sA < -CLEAR_M && sB > CLEAR_M))) return false;
+  const float t = sA / (sA - sB);
+  const v3<float> P = axpy(t, B - A, A) - O;
+  const float uu = dot(P, mk(f1.x, f1.y, f1.z)), vv = dot(P, mk(f2.x, f2.y, f2.z));
+  return uu > CLEAR_M && uu < f0.w - CLEAR_M && vv > CLEAR_M && vv < f1.w - CLEAR_M;
 }
 
+// Persistent grid over the first list; the occluders (records and boxes) are
+// staged in shared memory once per block.  Each occluder's box is loaded
+// once per candidate and tested against the boxes of all N + 1 segments.
 template <int N>
 __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevEnds ep, const float4* ends32,
                                                                CandView cv, SolView out, RefineList rl1,
                                                                RefineList rl2) {
+  extern __shared__ float4 occ_sm[];  // [6][n_occ]
   int64_t end = cv.order_begin[N];
   if (end > cv.cap) end = cv.cap;
   int64_t begin = cv.order_begin[N - 1];
   if (begin > end) begin = end;
   int64_t n = (int64_t)rl1.count[N - 1];
   if (n > end - begin) n = end - begin;
+  if ((int64_t)blockIdx.x * blockDim.x >= n) return;  // the whole block
+  const int no = sc.n_occ;
+  for (int q = threadIdx.x; q < 6 * no; q += blockDim.x)
+    occ_sm[q] = q < 4 * no ? __ldg(sc.c32 + q) : __ldg(sc.cbox + (q - 4 * no));
+  __syncthreads();
   const unsigned lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
@@ -506,9 +514,23 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
             P[k + 1] = point_at<float, false>(kind, r, d2f_bits(out.T[(int64_t)(2 * k) * out.cap + c]),
                                               d2f_bits(out.T[(int64_t)(2 * k + 1) * out.cap + c])).X;
           }
-          bool blocked = false;
+          v3<float> lo[N + 1], hi[N + 1];
 #pragma unroll
-          for (int j = 0; j <= N; ++j) blocked = blocked || clearly_blocked(sc, P[j], P[j + 1]);
+          for (int j = 0; j <= N; ++j) {
+            lo[j] = mk(fminf(P[j].x, P[j + 1].x), fminf(P[j].y, P[j + 1].y), fminf(P[j].z, P[j + 1].z));
+            hi[j] = mk(fmaxf(P[j].x, P[j + 1].x), fmaxf(P[j].y, P[j + 1].y), fmaxf(P[j].z, P[j + 1].z));
+          }
+          bool blocked = false;
+          for (int o = 0; o < no && !blocked; ++o) {
+            const float4 bl = occ_sm[4 * no + o], bh = occ_sm[5 * no + o];
+            if (bl.w != 0.f) continue;  // rectangles only
+#pragma unroll
+            for (int j = 0; j <= N; ++j) {
+              if (lo[j].x <= bh.x && hi[j].x >= bl.x && lo[j].y <= bh.y && hi[j].y >= bl.y && lo[j].z <= bh.z &&
+                  hi[j].z >= bl.z)
+                blocked = blocked || clearly_crosses(occ_sm, no, o, P[j], P[j + 1]);
+            }
+          }
           if (blocked) {
             out.status[c] = (uint8_t)(out.status[c] | MPT_PATH_PRESCREENED);
             keep = false;
@@ -528,29 +550,40 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
 }
 
 // ------------------------------------------------------------- kernel B --
-// Full FP64 Gauss-Newton with backtracking (the fallback of the refinement).
+// Gauss-Newton with backtracking entirely in float-float (the fallback of
+// the refinement for ill-conditioned paths).  Stops as soon as the cost is
+// below `stop` (the refinement target): float-float rounding puts a floor of
+// ~1e-26 under the cost, where further steps only chase rounding noise.  It
+// also stops at a local minimum with non-zero residual, where the model's
+// predicted decrease -g.dlt is below 1e-3 of the cost (a true path has the
+// prediction close to the whole cost), after 4 halvings of the step, and
+// after an accepted step that does not quarter the cost.
 template <int N>
-__device__ double gn64(const int (&kind)[N], const Rec<double> (&rec)[N], double (&prm)[2 * N],
-                       const v3<double>& A, const v3<double>& B, int max_iters, double mu) {
+__device__ ff gn_ff(const int (&kind)[N], const Rec<ff> (&rec)[N], ff (&prm)[2 * N], const v3<ff>& A,
+                    const v3<ff>& B, int max_iters, float mu, float stop) {
   constexpr int Q = 2 * N, P = Q * (Q + 1) / 2;
-  double jtj[P], g[Q], dlt[Q], trial[Q];
+  ff jtj[P], g[Q], dlt[Q], trial[Q];
   bool ok;
-  double cost = eval_path<N, double, double, true>(kind, rec, prm, A, B, jtj, g, ok);
-  if (!ok) return (double)INFINITY;
-  double alpha = 1.0;
+  ff cost = eval_path<N, ff, ff, true>(kind, rec, prm, A, B, jtj, g, ok);
+  if (!ok) return ff((float)INFINITY);
+  float alpha = 1.0f;
   bool need_factor = true;
-  for (int it = 0; it < 4 * max_iters && cost >= 1e-30; ++it) {
+  for (int it = 0; it < 2 * max_iters && cost.hi >= stop; ++it) {
     if (need_factor) {
-      pin_unused<N, double>(kind, jtj, g);
-      cholesky<Q, double>(jtj, mu);
-      chol_solve<Q, double>(jtj, g, dlt);
-      alpha = 1.0;
+      pin_unused<N, ff>(kind, jtj, g);
+      cholesky<Q, ff>(jtj, ff(mu));
+      chol_solve<Q, ff>(jtj, g, dlt);
+      float pred = 0.f;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) pred = fmaf(-g[i].hi, dlt[i].hi, pred);
+      if (pred < 1e-3f * cost.hi) break;
+      alpha = 1.0f;
       need_factor = false;
     }
 #pragma unroll
-    for (int i = 0; i < Q; ++i) trial[i] = fma(alpha, dlt[i], prm[i]);
-    double jt2[P], g2[Q];
-    const double ct = eval_path<N, double, double, true>(kind, rec, trial, A, B, jt2, g2, ok);
+    for (int i = 0; i < Q; ++i) trial[i] = fma_(ff(alpha), dlt[i], prm[i]);
+    ff jt2[P], g2[Q];
+    const ff ct = eval_path<N, ff, ff, true>(kind, rec, trial, A, B, jt2, g2, ok);
     if (ok && ct < cost) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) prm[i] = trial[i];
@@ -558,19 +591,33 @@ __device__ double gn64(const int (&kind)[N], const Rec<double> (&rec)[N], double
       for (int i = 0; i < P; ++i) jtj[i] = jt2[i];
 #pragma unroll
       for (int i = 0; i < Q; ++i) g[i] = g2[i];
+      // near a path Gauss-Newton gains orders of magnitude per step; a step
+      // that does not even quarter the cost has reached the rounding floor
+      const bool stagnant = ct.hi > 0.25f * cost.hi;
       cost = ct;
+      if (stagnant) break;
       need_factor = true;
     } else {
-      alpha *= 0.5;
-      if (alpha < 1.0 / 64.0) break;
+      alpha *= 0.5f;
+      if (alpha < 1.0f / 16.0f) break;
     }
   }
   return cost;
 }
 
+// One thread per listed candidate: up to refine_steps mixed steps (residual
+// and cost in float-float, Jacobian and solve in FP32) until the cost is
+// below 1e-24, extended by up to 6 steps while they still halve the cost.
+// A candidate still at or above 1e-22 (ill-conditioned, near an object
+// crease) is queued for k_refine_fb.  Both bounds sit above the float-float
+// rounding floor of the cost (1e-28 .. 1e-23, larger for short segments far
+// from the origin) and far below the acceptance threshold 1e-20.
+constexpr float REFINE_STOP = 1e-24f, REFINE_TARGET = 1e-22f;
+
 template <int N>
-__global__ void __launch_bounds__(SOLVE_BLOCK) k_refine(DevScene sc, DevEnds ep, CandView cv, SolView out,
-                                                        SolveCfg cfg, RefineList rl) {
+__global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? 3 : 1)) k_refine(DevScene sc, DevEnds ep, CandView cv,
+                                                                        SolView out, SolveCfg cfg, RefineList rl,
+                                                                        RefineList rl3) {
   constexpr int Q = 2 * N;
   int64_t end = cv.order_begin[N];
   if (end > cv.cap) end = cv.cap;
@@ -578,61 +625,115 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_refine(DevScene sc, DevEnds ep,
   if (begin > end) begin = end;
   int64_t n = (int64_t)rl.count[N - 1];
   if (n > end - begin) n = end - begin;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = begin + rl.idx[begin + i];
+  const ff stop(REFINE_STOP), target(REFINE_TARGET);
+  const unsigned lane = threadIdx.x & 31;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + threadIdx.x;
+    bool fallback = false;
+    int64_t c = 0;
+    if (i < n) {
+      c = begin + rl.idx[begin + i];
+      if (c >= begin && c < end) {
+        const Cand cd = decode(__ldg(cv.rec + c));
+        int it_, ir_;
+        pair_ends(ep, cd.pair, it_, ir_);
+        const v3<ff> A = load_end_ff(ep.tx, it_);
+        const v3<ff> B = load_end_ff(ep.rx, ir_);
+        int kind[N];
+        Rec<ff> rec[N];
+        ff T0[Q], T[Q];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          kind[k] = __ldg(sc.kind + cd.ids[k]);
+          rec[k] = load_obj_ff(sc, cd.ids[k]);
+        }
+#pragma unroll
+        for (int j = 0; j < Q; ++j) T[j] = T0[j] = ff_from_double(out.T[(int64_t)j * out.cap + c]);
+        float jtj[Q * (Q + 1) / 2], g[Q], dlt[Q];
+        bool ok;
+        ff cst = eval_path<N, ff, float, true>(kind, rec, T, A, B, jtj, g, ok);
+        ff prev = cst;
+        for (int s = 0; ok && cst >= stop; ++s) {
+          // beyond refine_steps, up to 6 more mixed steps while the target is
+          // not met and each step still halves the cost (slow linear
+          // convergence of ill-conditioned paths under the FP32 Jacobian)
+          if (s >= cfg.refine_steps && (s >= cfg.refine_steps + 6 || cst < target || !(cst.hi < 0.5f * prev.hi)))
+            break;
+          prev = cst;
+          pin_unused<N, float>(kind, jtj, g);
+          cholesky<Q, float>(jtj, cfg.mu32);
+          chol_solve<Q, float>(jtj, g, dlt);
+#pragma unroll
+          for (int j = 0; j < Q; ++j) T[j] = T[j] + ff(dlt[j]);
+          cst = eval_path<N, ff, float, true>(kind, rec, T, A, B, jtj, g, ok);
+        }
+        fallback = !ok || !(cst < target);
+        // the fallback starts from what is written here: the mixed result,
+        // or the FP32 result (with an infinite cost) when an evaluation failed
+#pragma unroll
+        for (int j = 0; j < Q; ++j) out.T[(int64_t)j * out.cap + c] = to_double(ok ? T[j] : T0[j]);
+        out.cost[c] = ok && finite_ff(cst) ? to_double(cst) : (double)INFINITY;
+        out.status[c] = (uint8_t)(out.status[c] | MPT_PATH_REFINED | (fallback ? MPT_PATH_FALLBACK : 0));
+      }
+    }
+    const unsigned fm = __ballot_sync(FULL, fallback);
+    if (fm) {
+      const int leader = __ffs(fm) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(rl3.count + (N - 1), (unsigned long long)__popc(fm));
+      base = __shfl_sync(FULL, base, leader);
+      if (fallback) rl3.idx[begin + (int64_t)base + __popc(fm & ((1u << lane) - 1u))] = (int32_t)(c - begin);
+    }
+  }
+}
+
+// The fallback of the refinement: float-float Gauss-Newton for the queued
+// candidates, one candidate per warp (lane 0) so that the few long serial
+// solves run side by side on as many SM sub-partitions as there are.
+template <int N>
+__global__ void __launch_bounds__(32) k_refine_fb(DevScene sc, DevEnds ep, CandView cv, SolView out, SolveCfg cfg,
+                                                  RefineList rl3) {
+  constexpr int Q = 2 * N;
+  if (threadIdx.x != 0) return;
+  int64_t end = cv.order_begin[N];
+  if (end > cv.cap) end = cv.cap;
+  int64_t begin = cv.order_begin[N - 1];
+  if (begin > end) begin = end;
+  int64_t n = (int64_t)rl3.count[N - 1];
+  if (n > end - begin) n = end - begin;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const int64_t c = begin + rl3.idx[begin + i];
     if (c < begin || c >= end) continue;
     const Cand cd = decode(__ldg(cv.rec + c));
     int it_, ir_;
     pair_ends(ep, cd.pair, it_, ir_);
-    const v3<double> A = mk(__ldg(ep.tx + 3 * it_), __ldg(ep.tx + 3 * it_ + 1), __ldg(ep.tx + 3 * it_ + 2));
-    const v3<double> B = mk(__ldg(ep.rx + 3 * ir_), __ldg(ep.rx + 3 * ir_ + 1), __ldg(ep.rx + 3 * ir_ + 2));
+    const v3<ff> A = load_end_ff(ep.tx, it_);
+    const v3<ff> B = load_end_ff(ep.rx, ir_);
     int kind[N];
-    Rec<double> rec[N];
-    double T[Q];
+    Rec<ff> rec[N];
+    ff T[Q];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       kind[k] = __ldg(sc.kind + cd.ids[k]);
-      rec[k] = load_obj64(sc, cd.ids[k]);
+      rec[k] = load_obj_ff(sc, cd.ids[k]);
     }
 #pragma unroll
-    for (int j = 0; j < Q; ++j) T[j] = out.T[(int64_t)j * out.cap + c];
-    // mixed steps: FP64 residual and cost, FP32 Jacobian and solve
-    float jtj[Q * (Q + 1) / 2], g[Q], dlt[Q];
-    bool ok;
-    double c64 = eval_path<N, double, float, true>(kind, rec, T, A, B, jtj, g, ok);
-    for (int s = 0; s < cfg.refine_steps && ok && c64 >= 1e-26; ++s) {
-      pin_unused<N, float>(kind, jtj, g);
-      cholesky<Q, float>(jtj, cfg.mu32);
-      chol_solve<Q, float>(jtj, g, dlt);
+    for (int j = 0; j < Q; ++j) T[j] = ff_from_double(out.T[(int64_t)j * out.cap + c]);
+    const double c1 = out.cost[c];
+    const ff c2 = gn_ff<N>(kind, rec, T, A, B, cfg.fallback_iters, (float)cfg.mu64, REFINE_TARGET);
+    if (finite_ff(c2) && to_double(c2) < c1) {
 #pragma unroll
-      for (int j = 0; j < Q; ++j) T[j] += f2d_bits(dlt[j]);
-      c64 = eval_path<N, double, float, true>(kind, rec, T, A, B, jtj, g, ok);
+      for (int j = 0; j < Q; ++j) out.T[(int64_t)j * out.cap + c] = to_double(T[j]);
+      out.cost[c] = to_double(c2);
     }
-    if (!ok || !(c64 < 1e-24)) {
-      // ill-conditioned: full FP64 Gauss-Newton from the better of the two points
-      double T0[Q];
-#pragma unroll
-      for (int j = 0; j < Q; ++j) T0[j] = ok ? T[j] : out.T[(int64_t)j * out.cap + c];
-      const double c2 = gn64<N>(kind, rec, T0, A, B, cfg.fallback_iters, cfg.mu64);
-      if (c2 < c64 || !ok) {
-#pragma unroll
-        for (int j = 0; j < Q; ++j) T[j] = T0[j];
-        c64 = c2;
-        ok = true;
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < Q; ++j) out.T[(int64_t)j * out.cap + c] = T[j];
-    out.cost[c] = ok ? c64 : (double)INFINITY;
-    out.status[c] = (uint8_t)(out.status[c] | MPT_PATH_REFINED);
   }
 }
 
 // ------------------------------------------------------------ launching --
 template <class K>
-static int grid_for(mpt_ctx* ctx, K kernel, const mpt_schedule* sch) {
+static int grid_for(mpt_ctx* ctx, K kernel, const mpt_schedule* sch, size_t smem = 0) {
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, SOLVE_BLOCK, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, SOLVE_BLOCK, smem);
   if (occ < 1) occ = 1;
   if (sch && sch->blocks_per_sm > 0 && sch->blocks_per_sm < occ) occ = sch->blocks_per_sm;
   return ctx->sms * occ;
@@ -643,8 +744,9 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
                        const SolView& sv, const SolveCfg& cfg, const mpt_schedule* sch, RefineList rl,
                        RefineList rl2, bool curved, cudaStream_t st) {
   // counters[0..3]: per-order candidate cursors; [4]: mixed-order cursor;
-  // [8..11]: refine list sizes; [12..15]: sizes after the visibility prescreen
-  MPT_CUDA_TRY(cudaMemsetAsync(ctx->counters, 0, 16 * sizeof(unsigned long long), st));
+  // [8..11]: refine list sizes; [12..15]: sizes after the visibility
+  // prescreen; [16..19]: fallback queue sizes
+  MPT_CUDA_TRY(cudaMemsetAsync(ctx->counters, 0, 20 * sizeof(unsigned long long), st));
   if (sch && sch->mixed_orders) {
     k_gn_mixed<PREC><<<grid_for(ctx, k_gn_mixed<PREC>, sch), SOLVE_BLOCK, 0, st>>>(sc, ep, ends32, cv, sv, cfg,
                                                                                   ctx->counters + 4, rl);
@@ -666,17 +768,24 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
 #undef MPT_LAUNCH_GN
   }
   if (PREC == MPT_FP32_FP64REFINE) {
-#define MPT_LAUNCH_VIS(N)                                                                                \
-  k_vis_prescreen<N><<<grid_for(ctx, k_vis_prescreen<N>, nullptr), SOLVE_BLOCK, 0, st>>>(sc, ep, ends32, cv, \
-                                                                                          sv, rl, rl2);     \
+    const size_t vsmem = (size_t)sc.n_occ * 96;
+#define MPT_LAUNCH_VIS(N)                                                                                   \
+  if (vsmem > 48 * 1024)                                                                                    \
+    cudaFuncSetAttribute(k_vis_prescreen<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem);      \
+  k_vis_prescreen<N><<<grid_for(ctx, k_vis_prescreen<N>, nullptr, vsmem), SOLVE_BLOCK, vsmem, st>>>(        \
+      sc, ep, ends32, cv, sv, rl, rl2);                                                                     \
   MPT_LAUNCH_CHECK();
     MPT_LAUNCH_VIS(1)
     MPT_LAUNCH_VIS(2)
     MPT_LAUNCH_VIS(3)
     MPT_LAUNCH_VIS(4)
 #undef MPT_LAUNCH_VIS
-#define MPT_LAUNCH_REF(N)                                                                                \
-  k_refine<N><<<grid_for(ctx, k_refine<N>, nullptr), SOLVE_BLOCK, 0, st>>>(sc, ep, cv, sv, cfg, rl2); \
+    // the fallback queue reuses the first list's storage (read by then)
+    const RefineList rl3{ctx->counters + 16, rl.idx};
+#define MPT_LAUNCH_REF(N)                                                                                   \
+  k_refine<N><<<grid_for(ctx, k_refine<N>, nullptr), SOLVE_BLOCK, 0, st>>>(sc, ep, cv, sv, cfg, rl2, rl3); \
+  MPT_LAUNCH_CHECK();                                                                                       \
+  k_refine_fb<N><<<ctx->sms * 4, 32, 0, st>>>(sc, ep, cv, sv, cfg, rl3);                                    \
   MPT_LAUNCH_CHECK();
     MPT_LAUNCH_REF(1)
     MPT_LAUNCH_REF(2)
@@ -698,7 +807,7 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
   cfg.localmin_cost = 1e-3f;
   cfg.localmin_ratio = 1e-4f;
   cfg.refine_steps = (sch && sch->refine_steps > 0) ? (sch->refine_steps > 4 ? 4 : sch->refine_steps) : 2;
-  cfg.fallback_iters = 8;
+  cfg.fallback_iters = 4;  // at most 8 evaluations
   const double S = scene->d.scale;
   cfg.c_tol32 = 1e-12f;
   cfg.step_tol32 = (float)(1e-6 * S);

@@ -22,7 +22,7 @@ P, I32, I64, U64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
 MPT_OK, MPT_ERR_ARG, MPT_ERR_CUDA, MPT_ERR_CAPACITY, MPT_ERR_TIMEOUT, MPT_ERR_UNSUPPORTED = range(6)
 FP64_PLAIN, FP32, FP32_FP64REFINE = 0, 1, 2
 PATH_CONVERGED, PATH_MAXITER, PATH_DIVERGED, PATH_STALLED, PATH_NONFINITE = range(5)
-PATH_REFINED, PATH_PRESCREENED = 0x10, 0x20
+PATH_REFINED, PATH_PRESCREENED, PATH_FALLBACK = 0x10, 0x20, 0x40
 TAU = 1e-20  # acceptance threshold on the cost of Eq. 15
 
 
