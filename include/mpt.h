@@ -167,12 +167,15 @@ typedef struct {
 
 /* Solver schedule; NULL selects the library's defaults for the device. */
 typedef struct {
-  int32_t block;          /* threads per block (multiple of 32, <= 1024) */
-  int32_t blocks_per_sm;  /* resident blocks per SM for the persistent grid */
-  int32_t tile;           /* candidates per work-stealing tile (multiple of block) */
-  int32_t max_iters;      /* minimiser iteration cap (<= 255) */
-  int32_t refine_steps;   /* FP64 refinement steps (1 or 2) */
+  int32_t block;          /* reserved (the solver's blocks have 128 threads) */
+  int32_t blocks_per_sm;  /* resident blocks per SM for the persistent grid (0: all that fit) */
+  int32_t tile;           /* candidates a warp claims at once, 32..128 (0: 128); claims
+                             shrink towards 32 as the range runs out */
+  int32_t max_iters;      /* minimiser iteration cap (<= 160; 0: 24) */
+  int32_t refine_steps;   /* mixed-precision refinement steps (1..4; 0: 2) */
   int32_t mixed_orders;   /* 1: one launch over all orders; 0: one launch per order */
+  int32_t refill_min;     /* idle lanes of a warp that trigger taking new candidates
+                             (1..32; 0: 12) */
 } mpt_schedule;
 
 /* Compacted valid paths (caller-owned device buffers). */
@@ -231,7 +234,7 @@ int64_t mpt_candidate_count(const mpt_scene* scene, const mpt_endpoints* ends, i
  * (divided by ||X_k - X_{k-1}||) and Eq. 9.  Reads min(*cand->count,
  * cand->capacity) candidates on the device.  precision: MPT_FP64_PLAIN,
  * MPT_FP32 or MPT_FP32_FP64REFINE.  out->capacity must be >= cand->capacity
- * (MPT_ERR_CAPACITY otherwise). */
+ * and cand->capacity below 2^31 (MPT_ERR_CAPACITY otherwise). */
 int mpt_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
               const mpt_candidates* cand, int precision, const mpt_schedule* schedule,
               mpt_solutions* out, void* stream);

@@ -307,6 +307,7 @@ int mpt_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, c
   if (schedule && (schedule->max_iters < 0 || schedule->refine_steps < 0 || schedule->blocks_per_sm < 0))
     return MPT_ERR_ARG;
   if (out->capacity < cand->capacity) return MPT_ERR_CAPACITY;
+  if (cand->capacity > INT32_MAX) return MPT_ERR_CAPACITY;  // per-order offsets are 32-bit
   if (cand->capacity == 0) return MPT_OK;
   return launch_solve(ctx, scene, ends, cand, precision, schedule, out, reinterpret_cast<cudaStream_t>(stream));
 }

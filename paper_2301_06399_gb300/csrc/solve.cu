@@ -4,22 +4,20 @@
 // Kernel A (k_gn): a persistent grid per path order.  Each lane runs a small
 // state machine; every pass of the loop performs exactly one evaluation
 // (cost + normal equations at the lane's trial point) and then accepts,
-// backtracks or finishes.  A lane that finishes writes its result and
-// immediately takes the next candidate of its warp's chunk (a warp claims 256
-// consecutive candidates at a time from a per-order counter, so its lanes
-// share one object sequence and take the same branches), so lanes stay busy
+// backtracks or finishes.  Lanes that finish take the next candidates of
+// their warp's piece of the range (consecutive candidates, so the lanes share
+// one object sequence and take the same branches), so lanes stay busy
 // although candidates converge after different numbers of iterations.  No
 // block-level barriers.  Endpoints are read from FP32 copies and results are
 // widened to FP64 on the integer units: the FP64 pipe stays idle.
 //
 // Kernel B (k_refine, MPT_FP32_FP64REFINE only): candidates whose FP32 cost
-// is below 1e-6 and whose parameters lie within 0.1 m of their bounds are
-// appended by kernel A to a per-order list; kernel B takes up to
-// `refine_steps` Gauss-Newton steps with the residual and cost in FP64 and
-// the Jacobian in FP32, and falls back to full FP64 Gauss-Newton (FP64
-// Jacobian, backtracking) when the cost is still above 1e-24 (ill-
-// conditioned paths near object creases).  Every other candidate is rejected
-// by validation whatever its last digits, so it keeps its FP32 result.
+// is below 1e-6, whose parameters lie within 0.1 m of their bounds and that
+// the visibility prescreen does not reject are refined with mixed steps
+// (residual and cost in float-float, Jacobian in FP32); ill-conditioned ones
+// (near object creases) go on to float-float Gauss-Newton (k_refine_fb).
+// Every other candidate is rejected by validation whatever its last digits,
+// so it keeps its FP32 result.
 //
 // MPT_FP64_PLAIN runs kernel A in FP64 (the plain GPU method); MPT_FP32 runs
 // kernel A only.
@@ -32,8 +30,9 @@ namespace mpt {
 
 struct SolveCfg {
   int max_iters, max_evals;
+  int refill_min, piece;
   int refine_steps, fallback_iters;
-  float min_alpha, localmin_cost, localmin_ratio;
+  float min_alpha, localmin_cost, localmin_ratio, localmin_ratio_planar;
   float c_tol32, step_tol32;
   double c_tol64, step_tol64;
   double diverge;
@@ -179,67 +178,127 @@ __device__ __forceinline__ uint64_t pack_ids(const Cand& cd, int n) {
 
 // ------------------------------------------------------------- kernel A --
 // The lanes of one warp solve the candidates of order N in [begin, end).
-// With a counter, the warp claims CHUNK-sized pieces of the range as it goes
-// (work stealing between warps); without one it takes [begin, end) as its
-// single chunk.  order_base = first candidate of order N (refine-list base).
+// With a counter, the warp claims pieces of the range as it goes (work
+// stealing between warps); without one it walks [begin, end) piece by
+// piece.  order_base = first candidate of order N (refine-list base).
+//
+// Candidate records are staged in shared memory: every claimed piece is
+// copied there by cp.async (16 bytes per lane per copy) one piece ahead of
+// its use, so that taking a new candidate costs a shared-memory read
+// instead of a DRAM round trip.  Object records and endpoints are read from
+// global memory (L1-resident, the same address for the lanes of a warp) at
+// every evaluation instead of being held in registers across iterations.
 //
 // A lane that finishes keeps its result and goes idle; idle lanes write their
-// results and take new candidates together, once REFILL_MIN of them are idle
-// (or nothing else is running), so the narrow write/refill code runs for many
-// lanes at once instead of once per finishing lane.
-constexpr int REFILL_MIN = 8;
+// results and take new candidates together, once cfg.refill_min of them are
+// idle (or nothing else is running), so the narrow write/refill code runs for
+// many lanes at once instead of once per finishing lane.
+//
+// Pieces are cfg.piece candidates while the range is long and shrink to 32
+// as it runs out (guided self-scheduling: about half of what is left, split
+// over every warp), so that warps run out of work at nearly the same time.
+constexpr int GN_CHUNK = 128;  // records per staged piece (the largest piece)
+constexpr int GN_WARPS = SOLVE_BLOCK / 32;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
+}
+
+template <int N, class R>
+__device__ __forceinline__ void load_objs(const DevScene& sc, uint32_t ids01, uint32_t ids23, Rec<R> (&rec)[N]) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const uint32_t w = k < 2 ? ids01 : ids23;
+    rec[k] = load_obj<R>(sc, (int)((w >> (16 * (k & 1))) & 0xFFFFu));
+  }
+}
 
 template <int N, int PREC, bool CURVED>
 __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, const float4* ends32,
                                         const CandView& cv, const SolView& out, const SolveCfg& cfg,
                                         unsigned long long* counter, const RefineList& rl, int64_t begin,
-                                        int64_t end, int64_t order_base) {
+                                        int64_t end, int64_t order_base, uint4 (*rbuf)[GN_CHUNK]) {
   using R = typename std::conditional<PREC == MPT_FP64_PLAIN, double, float>::type;
   constexpr int Q = 2 * N, P = Q * (Q + 1) / 2;
   const unsigned lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const R c_tol = R(PREC == MPT_FP64_PLAIN ? cfg.c_tol64 : cfg.c_tol32);
-  const R step_tol = R(PREC == MPT_FP64_PLAIN ? cfg.step_tol64 : cfg.step_tol32);
+  const R c_tol = R(PREC == MPT_FP64_PLAIN ? cfg.c_tol64 : (double)cfg.c_tol32);
+  const R step_tol = R(PREC == MPT_FP64_PLAIN ? cfg.step_tol64 : (double)cfg.step_tol32);
   const R diverge = R(cfg.diverge);
-  const R mu = R(PREC == MPT_FP64_PLAIN ? cfg.mu64 : cfg.mu32);
+  const R mu = R(PREC == MPT_FP64_PLAIN ? cfg.mu64 : (double)cfg.mu32);
 
-  int64_t c = -1;       // candidate being solved, -1 = idle
-  int64_t done_c = -1;  // finished candidate whose result is not written yet
+  // per lane: candidate c (offset from begin; -1 = idle) and its data
+  int c = -1;
+  int done_c = -1;  // finished candidate whose result is not written yet
   int done_status = 0;
   bool done_push = false;
   bool exhausted = false;
-  int kind[N];
-  Rec<R> rec[N];
-  v3<R> A, B;
+  uint32_t ids01 = 0, ids23 = 0;  // object ids, 16 bits each
+  int kinds = 0;                  // object kinds, 8 bits each
+  int it_ = 0, ir_ = 0;
   R prm[Q], trial[Q], dlt[Q];
   R cost = R(0), alpha = R(1);
+  R lm_ratio = R(cfg.localmin_ratio_planar);  // local-minimum test of this sequence
   int iters = 0, evals = 0;
   bool fresh = false;
 
-  // warp-uniform cursor into the warp's current chunk of candidates: lanes
-  // refill from consecutive candidates, so they share one object sequence
-  int64_t chunk_cur = 0, chunk_end = 0;
-  bool range_done = false;
-  if (counter == nullptr) {
-    chunk_cur = begin;
-    chunk_end = end;
-    range_done = true;
-  }
+  // ---- warp-uniform staging of candidate records: the current piece (being
+  // taken from) and the next one (in flight)
+  int64_t walk = begin;  // past the last piece seen
+  const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  auto claim = [&](int64_t& base, int& len) {
+    int size = cfg.piece;
+    if (counter != nullptr) {
+      // guided size from the last position seen (a slight lag is harmless)
+      const int64_t guided = (end - walk) / (2 * n_warps);
+      if (guided < size) size = guided < 32 ? 32 : (int)guided;
+      unsigned long long b = 0;
+      if (lane == 0) b = atomicAdd(counter, (unsigned long long)size);
+      b = __shfl_sync(FULL, b, 0);
+      base = begin + (int64_t)b;
+      walk = base + size;
+    } else {
+      base = walk;
+      walk += size;
+    }
+    len = base < end ? (int)(end - base < size ? end - base : size) : 0;
+  };
+  auto stage = [&](int b, int64_t base, int len) {
+    for (int k = lane; k < len; k += 32) cp_async16(&rbuf[b][k], cv.rec + base + k);
+    cp_async_commit();
+  };
+  int buf = 0;
+  int64_t cur_base, nxt_base;
+  int cur_len, nxt_len, cur_pos = 0;
+  claim(cur_base, cur_len);
+  stage(0, cur_base, cur_len);
+  claim(nxt_base, nxt_len);
+  stage(1, nxt_base, nxt_len);
+  cp_async_wait<1>();
+  __syncwarp();
+
   for (;;) {
     const unsigned idle = __ballot_sync(FULL, c < 0);
-    if (idle == FULL || __popc(idle) >= REFILL_MIN) {
+    if (idle == FULL || __popc(idle) >= cfg.refill_min) {
       // ---- write the results waiting in idle lanes
       if (done_c >= 0) {
+        const int64_t dc = begin + done_c;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) out.T[(int64_t)i * out.cap + done_c] = to_f64(prm[i]);
+        for (int i = 0; i < Q; ++i) out.T[(int64_t)i * out.cap + dc] = to_f64(prm[i]);
         if (out.T32 != nullptr) {
 #pragma unroll
-          for (int i = 0; i < Q; ++i) out.T32[(int64_t)i * out.cap + done_c] = (float)prm[i];
+          for (int i = 0; i < Q; ++i) out.T32[(int64_t)i * out.cap + dc] = (float)prm[i];
         }
-        out.cost[done_c] = to_f64(cost);
-        out.status[done_c] = (uint8_t)done_status;
-        out.iters[done_c] = (uint8_t)min(iters, 255);
-        out.evals[done_c] = (uint8_t)min(evals, 255);
+        out.cost[dc] = to_f64(cost);
+        out.status[dc] = (uint8_t)done_status;
+        out.iters[dc] = (uint8_t)min(iters, 255);
+        out.evals[dc] = (uint8_t)min(evals, 255);
       }
       if (PREC == MPT_FP32_FP64REFINE) {
         const unsigned pm = __ballot_sync(FULL, done_push);
@@ -250,50 +309,56 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
           base = __shfl_sync(FULL, base, leader);
           if (done_push) {
             const int64_t pos = (int64_t)base + __popc(pm & lt_mask);
-            rl.idx[order_base + pos] = (int32_t)(done_c - order_base);
+            rl.idx[order_base + pos] = (int32_t)(begin + done_c - order_base);
           }
         }
       }
       done_c = -1;
       done_push = false;
-      // ---- take the next candidates of the warp's chunk
+      // ---- take the next candidates from the staged pieces
       bool need = (c < 0) && !exhausted;
       unsigned need_mask = __ballot_sync(FULL, need);
       while (need_mask) {
-        if (chunk_cur >= chunk_end) {
-          if (range_done) break;
-          unsigned long long base = 0;
-          if (lane == 0) base = atomicAdd(counter, (unsigned long long)CHUNK);
-          base = __shfl_sync(FULL, base, 0);
-          chunk_cur = begin + (int64_t)base;
-          chunk_end = chunk_cur + CHUNK < end ? chunk_cur + CHUNK : end;
-          if (chunk_cur >= end) {
-            range_done = true;
-            break;
-          }
+        if (cur_pos >= cur_len) {
+          if (nxt_len == 0) break;  // the range is done
+          // the next piece becomes current; stage the one after it
+          buf ^= 1;
+          cur_base = nxt_base;
+          cur_len = nxt_len;
+          cur_pos = 0;
+          cp_async_wait<0>();
+          __syncwarp();
+          claim(nxt_base, nxt_len);
+          stage(buf ^ 1, nxt_base, nxt_len);
         }
-        const int avail = (int)(chunk_end - chunk_cur);
+        const int avail = cur_len - cur_pos;
+        const int nneed = __popc(need_mask);
         const int rank = __popc(need_mask & lt_mask);
         const bool take = need && rank < avail;
-        const int64_t idx = chunk_cur + rank;
-        const int served = __popc(need_mask) < avail ? __popc(need_mask) : avail;
-        chunk_cur += served;
+        const int slot = cur_pos + rank;
+        cur_pos += nneed < avail ? nneed : avail;
         if (take) {
           need = false;
-          const Cand cd = decode(__ldg(cv.rec + idx));
+          const int64_t idx = cur_base + slot;
+          const uint4 rr = rbuf[buf][slot];
+          const Cand cd = decode(rr);
           if (cand_in_range(sc, ep, cd) && cd.order == N) {
-            c = idx;
-            int it_, ir_;
+            c = (int)(idx - begin);
             pair_ends(ep, cd.pair, it_, ir_);
-            A = load_end<R>(ep.tx, ends32, it_);
-            B = load_end<R>(ep.rx, ends32 + ep.n_tx, ir_);
+            ids01 = rr.y;
+            ids23 = rr.z;
+            const v3<R> A = load_end<R>(ep.tx, ends32, it_);
+            const v3<R> B = load_end<R>(ep.rx, ends32 + ep.n_tx, ir_);
             const uint64_t packed = pack_ids(cd, N);
+            kinds = 0;
+            lm_ratio = R(cfg.localmin_ratio_planar);
 #pragma unroll
             for (int k = 0; k < N; ++k) {
-              kind[k] = __ldg(sc.kind + cd.ids[k]);
-              rec[k] = load_obj<R>(sc, cd.ids[k]);
-              init_params<R>(kind[k], rec[k], (2 * k < N) ? A : B, cv.init_seed, cd.pair, packed, cd.start, k,
-                             trial[2 * k], trial[2 * k + 1]);
+              const int kd = __ldg(sc.kind + cd.ids[k]);
+              kinds |= kd << (8 * k);
+              if (kd == K_PARAB || kd == K_ARC) lm_ratio = R(cfg.localmin_ratio);
+              init_params<R>(kd, load_obj<R>(sc, cd.ids[k]), (2 * k < N) ? A : B, cv.init_seed, cd.pair, packed,
+                             cd.start, k, trial[2 * k], trial[2 * k + 1]);
             }
             fresh = true;
             iters = 0;
@@ -308,7 +373,7 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
         }
         need_mask = __ballot_sync(FULL, need);
       }
-      if (range_done && c < 0) exhausted = true;
+      if (cur_pos >= cur_len && nxt_len == 0 && c < 0) exhausted = true;
     }
     if (__ballot_sync(FULL, c >= 0) == 0) {
       if (__ballot_sync(FULL, !exhausted || done_c >= 0) == 0) break;
@@ -316,6 +381,13 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
     }
     if (c >= 0) {
       // ---- one evaluation at the trial point
+      int kind[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) kind[k] = (kinds >> (8 * k)) & 0xFF;
+      Rec<R> rec[N];
+      load_objs<N, R>(sc, ids01, ids23, rec);
+      const v3<R> A = load_end<R>(ep.tx, ends32, it_);
+      const v3<R> B = load_end<R>(ep.rx, ends32 + ep.n_tx, ir_);
       R jtj[P], g[Q];
       bool ok;
       const R ct = eval_path<N, R, R, true, CURVED>(kind, rec, trial, A, B, jtj, g, ok);
@@ -355,13 +427,14 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
         chol_solve<Q, R>(jtj, g, dlt);
         alpha = R(1);
         // The Gauss-Newton model predicts the decrease -g.dlt; when it is a
-        // negligible fraction of a large cost the iterate sits at a local
-        // minimum with non-zero residual: no path of this sequence is near.
+        // small fraction of a large cost the iterate sits at a local minimum
+        // with non-zero residual: no path of this sequence is near.  The
+        // fraction is 0.1 for planes and straight edges, 1e-4 when a
+        // paraboloid or an arc bends the cost away from its model.
         R pred = R(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) pred = fma_(-g[i], dlt[i], pred);
-        if (iters >= 2 && cost > R(cfg.localmin_cost) && pred < R(cfg.localmin_ratio) * cost)
-          done = MPT_PATH_STALLED;
+        if (iters >= 2 && cost > R(cfg.localmin_cost) && pred < lm_ratio * cost) done = MPT_PATH_STALLED;
       }
       if (done < 0) {
 #pragma unroll
@@ -385,19 +458,22 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
       }
     }
   }
+  cp_async_wait<0>();  // nothing left in flight when the warp leaves
+  __syncwarp();
 }
 
-// Orders 1-2 (the bulk of the work) are held to 128 registers: 4 blocks of
-// 128 threads per SM.
+// Orders 1-2 (the bulk of the work) of the FP32 solver are held to 102
+// registers: 5 blocks of 128 threads per SM.
 template <int N, int PREC, bool CURVED>
-__global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? 4 : 1)) k_gn(DevScene sc, DevEnds ep, const float4* ends32, CandView cv,
-                                                    SolView out, SolveCfg cfg, unsigned long long* counter,
-                                                    RefineList rl) {
+__global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? (PREC == MPT_FP64_PLAIN ? 2 : 5) : 1))
+    k_gn(DevScene sc, DevEnds ep, const float4* ends32, CandView cv, SolView out, SolveCfg cfg,
+         unsigned long long* counter, RefineList rl) {
+  __shared__ __align__(16) uint4 rbuf[GN_WARPS][2][GN_CHUNK];
   int64_t end = cv.order_begin[N];
   if (end > cv.cap) end = cv.cap;
   int64_t begin = cv.order_begin[N - 1];
   if (begin > end) begin = end;
-  gn_warp<N, PREC, CURVED>(sc, ep, ends32, cv, out, cfg, counter, rl, begin, end, begin);
+  gn_warp<N, PREC, CURVED>(sc, ep, ends32, cv, out, cfg, counter, rl, begin, end, begin, rbuf[threadIdx.x >> 5]);
 }
 
 // One launch over every order (uneven orders and convergence in one
@@ -410,6 +486,7 @@ template <int PREC>
 __global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_mixed(DevScene sc, DevEnds ep, const float4* ends32,
                                                           CandView cv, SolView out, SolveCfg cfg,
                                                           unsigned long long* counter, RefineList rl) {
+  __shared__ __align__(16) uint4 rbuf[GN_WARPS][2][GN_CHUNK];
   int64_t total = cv.order_begin[4];
   if (total > cv.cap) total = cv.cap;
   const unsigned lane = threadIdx.x & 31;
@@ -427,10 +504,10 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_mixed(DevScene sc, DevEnds e
       if (oe <= s) oe = s + 1;
       const int64_t ob = (o >= 1 && o <= 4) ? cv.order_begin[o - 1] : 0;
       switch (o) {
-        case 1: gn_warp<1, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
-        case 2: gn_warp<2, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
-        case 3: gn_warp<3, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
-        case 4: gn_warp<4, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob); break;
+        case 1: gn_warp<1, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob, rbuf[threadIdx.x >> 5]); break;
+        case 2: gn_warp<2, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob, rbuf[threadIdx.x >> 5]); break;
+        case 3: gn_warp<3, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob, rbuf[threadIdx.x >> 5]); break;
+        case 4: gn_warp<4, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob, rbuf[threadIdx.x >> 5]); break;
         default:
           if (lane == 0) {
             out.cost[s] = (double)INFINITY;
@@ -805,8 +882,11 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
   cfg.max_evals = cfg.max_iters * 5 / 3;
   cfg.min_alpha = 1.0f / 16.0f;
   cfg.localmin_cost = 1e-3f;
-  cfg.localmin_ratio = 1e-4f;
+  cfg.localmin_ratio = 1e-4f;         // sequences with a paraboloid or an arc edge
+  cfg.localmin_ratio_planar = 0.1f;   // planes and straight edges only
   cfg.refine_steps = (sch && sch->refine_steps > 0) ? (sch->refine_steps > 4 ? 4 : sch->refine_steps) : 2;
+  cfg.refill_min = (sch && sch->refill_min > 0) ? (sch->refill_min > 32 ? 32 : sch->refill_min) : 12;
+  cfg.piece = (sch && sch->tile > 0) ? (sch->tile < 32 ? 32 : (sch->tile > GN_CHUNK ? GN_CHUNK : sch->tile)) : GN_CHUNK;
   cfg.fallback_iters = 4;  // at most 8 evaluations
   const double S = scene->d.scale;
   cfg.c_tol32 = 1e-12f;
