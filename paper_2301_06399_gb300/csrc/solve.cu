@@ -887,7 +887,7 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
   cfg.refine_steps = (sch && sch->refine_steps > 0) ? (sch->refine_steps > 4 ? 4 : sch->refine_steps) : 2;
   cfg.refill_min = (sch && sch->refill_min > 0) ? (sch->refill_min > 32 ? 32 : sch->refill_min) : 12;
   cfg.piece = (sch && sch->tile > 0) ? (sch->tile < 32 ? 32 : (sch->tile > GN_CHUNK ? GN_CHUNK : sch->tile)) : GN_CHUNK;
-  cfg.fallback_iters = 4;  // at most 8 evaluations
+  cfg.fallback_iters = 2;  // at most 5 evaluations
   const double S = scene->d.scale;
   cfg.c_tol32 = 1e-12f;
   cfg.step_tol32 = (float)(1e-6 * S);
