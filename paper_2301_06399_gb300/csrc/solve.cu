@@ -23,6 +23,7 @@
 // kernel A only.
 #include <type_traits>
 
+#include "eval_f2.cuh"
 #include "ff.cuh"
 #include "mpt_internal.cuh"
 
@@ -390,7 +391,11 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
       const v3<R> B = load_end<R>(ep.rx, ends32 + ep.n_tx, ir_);
       R jtj[P], g[Q];
       bool ok;
-      const R ct = eval_path<N, R, R, true, CURVED>(kind, rec, trial, A, B, jtj, g, ok);
+      R ct;
+      if constexpr (std::is_same<R, float>::value)
+        ct = eval_path_f2<N, CURVED>(kind, rec, trial, A, B, jtj, g, ok);
+      else
+        ct = eval_path<N, R, R, true, CURVED>(kind, rec, trial, A, B, jtj, g, ok);
       ++evals;
       int done = -1;
       bool factor = false;
