@@ -171,6 +171,12 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
       o32[((size_t)(i / 4) * no + o) * 4 + (i % 4)] = (float)ov[(size_t)16 * o + i];
       o64[((size_t)(i / 2) * no + o) * 2 + (i % 2)] = ov[(size_t)16 * o + i];
     }
+  // object-major FP32 copy (the 64 bytes of object o contiguous) for the
+  // solver, which reloads the records of its sequence at every evaluation:
+  // one base address per object, the four float4 at constant offsets
+  std::vector<float> a32((size_t)no * 16);
+  for (int o = 0; o < no; ++o)
+    for (int i = 0; i < 16; ++i) a32[(size_t)16 * o + i] = (float)ov[(size_t)16 * o + i];
   for (int o = 0; o < nc; ++o)
     for (int i = 0; i < 16; ++i) {
       c32[((size_t)(i / 4) * nc + o) * 4 + (i % 4)] = (float)cv[(size_t)16 * o + i];
@@ -231,8 +237,9 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   const size_t s_kind = align256((size_t)no * 4), s_o32 = align256((size_t)no * 64),
                s_o64 = align256((size_t)no * 128), s_ck = align256((size_t)nc * 4 + 4),
                s_c32 = align256((size_t)nc * 64 + 16), s_c64 = align256((size_t)nc * 128 + 16),
-               s_oo = align256((size_t)no * 4), s_cb = align256((size_t)nc * 32 + 16);
-  const size_t total = s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb;
+               s_oo = align256((size_t)no * 4), s_cb = align256((size_t)nc * 32 + 16),
+               s_a32 = align256((size_t)no * 64);
+  const size_t total = s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb + s_a32;
   MPT_CUDA_TRY(cudaSetDevice(ctx->device));
   void* mem = nullptr;
   MPT_CUDA_TRY(cudaMalloc(&mem, total));
@@ -261,6 +268,7 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   d.c64 = reinterpret_cast<const double2*>(put(c64.data(), (size_t)nc * 128, s_c64));
   d.obj_occ = reinterpret_cast<const int32_t*>(put(obj_occ.data(), (size_t)no * 4, s_oo));
   d.cbox = reinterpret_cast<const float4*>(put(cbox.data(), (size_t)nc * 32, s_cb));
+  d.a32 = reinterpret_cast<const float4*>(put(a32.data(), (size_t)no * 64, s_a32));
   d.scale = desc->scale;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

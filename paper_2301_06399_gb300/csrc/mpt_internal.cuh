@@ -20,6 +20,7 @@ struct DevScene {
   int n_obj, n_occ;
   const int32_t* kind;      // [n_obj]
   const float4* o32;        // [4][n_obj]
+  const float4* a32;        // [n_obj][4]: the same FP32 records, object-major
   const double2* o64;       // [8][n_obj]
   const int32_t* occ_kind;  // [n_occ]
   const float4* c32;        // [4][n_occ]
@@ -66,6 +67,16 @@ __device__ __forceinline__ Rec<float> load_obj32(const DevScene& s, int o) {
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
     float4 q = __ldg(&s.o32[f * s.n_obj + o]);
+    r.v[4 * f] = q.x; r.v[4 * f + 1] = q.y; r.v[4 * f + 2] = q.z; r.v[4 * f + 3] = q.w;
+  }
+  return r;
+}
+__device__ __forceinline__ Rec<float> load_obj32a(const DevScene& s, int o) {
+  Rec<float> r;
+  const float4* p = s.a32 + 4 * o;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    float4 q = __ldg(p + f);
     r.v[4 * f] = q.x; r.v[4 * f + 1] = q.y; r.v[4 * f + 2] = q.z; r.v[4 * f + 3] = q.w;
   }
   return r;

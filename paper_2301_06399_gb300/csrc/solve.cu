@@ -96,7 +96,7 @@ __device__ __forceinline__ double to_f64(double x) { return x; }
 template <class R>
 __device__ __forceinline__ Rec<R> load_obj(const DevScene& s, int o);
 template <>
-__device__ __forceinline__ Rec<float> load_obj<float>(const DevScene& s, int o) { return load_obj32(s, o); }
+__device__ __forceinline__ Rec<float> load_obj<float>(const DevScene& s, int o) { return load_obj32a(s, o); }
 template <>
 __device__ __forceinline__ Rec<double> load_obj<double>(const DevScene& s, int o) { return load_obj64(s, o); }
 
