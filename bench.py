@@ -288,6 +288,20 @@ def run_ours(args):
             stream.synchronize()
             fp64_ms.append(a.elapsed_time(b))
         n_valid_fp64 = paths.n()
+
+        # ---- the FP32 minimiser alone (MPT_FP32: endpoint copy + k_gn per
+        # order, no prescreen or refinement), for the roofline of the
+        # dominant kernel
+        mini_ms = []
+        for i in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mpt.solve(ds, cands, mpt.FP32, out=sols, stream=stream)
+            b.record(stream)
+            stream.synchronize()
+            mini_ms.append(a.elapsed_time(b))
+        mini_flops = algorithmic_flops(mpt, sc, cands, sols, n_cand)
         # restore the FP32 state for the e2e leg
         step()
         stream.synchronize()
@@ -357,6 +371,10 @@ def run_ours(args):
                      "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {SM_MAX_MHZ_NOMINAL:.0f} MHz (derived)",
                      "solve_ms": solve_avg_ms, "fp32_flops_per_launch": flops,
+                     "fp32_minimiser": {"kernel": "k_gn orders 1-4 alone (MPT_FP32 solve: no prescreen or refinement)",
+                                        "ms": float(np.median(mini_ms)), "fp32_flops": mini_flops,
+                                        "achieved": mini_flops / (float(np.median(mini_ms)) * 1e-3) / 1e12,
+                                        "frac": mini_flops / (float(np.median(mini_ms)) * 1e-3) / 1e12 / peak_max},
                      "traffic": profile_traffic("mpt_solve") if args.rx_side == 32 else None},
         "fp64_plain": {"ms_per_step": float(np.median(fp64_ms)),
                        "value": n_cand * ws / (float(np.median(fp64_ms)) * 1e-3), "unit": UNIT,
