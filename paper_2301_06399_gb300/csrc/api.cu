@@ -183,17 +183,57 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
       c64[((size_t)(i / 2) * nc + o) * 2 + (i % 2)] = cv[(size_t)16 * o + i];
     }
   // plane objects whose rectangle is also an occluder
-  std::vector<int32_t> obj_occ(no, -1);
+  // Rectangles that hold every point an object can put on a path: for a
+  // plane, rectangles in the same plane (its own rectangle first); for a
+  // straight edge, rectangles whose plane contains both ends of the edge
+  // (the faces that meet at it).  A segment that ends on such a plane cannot
+  // cross it strictly (the visibility rule needs both ends more than 1e-6 m
+  // off the plane), so validation skips them; up to 4 per object.
+  std::vector<int32_t> obj_occ((size_t)no * 4, -1);
+  auto plane_dist = [&](const double* q, const double* X) {
+    return (X[0] - q[0]) * q[12] + (X[1] - q[1]) * q[13] + (X[2] - q[2]) * q[14];
+  };
   for (int o = 0; o < no; ++o) {
-    if (desc->obj_kind[o] != MPT_PLANE) continue;
+    const int kind = desc->obj_kind[o];
+    if (kind != MPT_PLANE && kind != MPT_LINE_EDGE) continue;
     const double* a = &ov[(size_t)16 * o];
+    int n_own = 0;
+    auto add_own = [&](int q) {
+      if (n_own < 4) obj_occ[(size_t)4 * o + n_own++] = q;
+    };
+    if (kind == MPT_PLANE) {
+      for (int q = 0; q < nc; ++q) {
+        if (desc->occ_kind[q] != MPT_OCC_RECT) continue;
+        const double* b = &cv[(size_t)16 * q];
+        // same corner, axes and extents (values 0..10 of both records)
+        bool same = true;
+        for (int i = 0; i < 11; ++i) same = same && a[i] == b[i];
+        if (same) { add_own(q); break; }
+      }
+    }
     for (int q = 0; q < nc; ++q) {
       if (desc->occ_kind[q] != MPT_OCC_RECT) continue;
+      if (n_own > 0 && obj_occ[(size_t)4 * o] == q) continue;
       const double* b = &cv[(size_t)16 * q];
-      // same corner, axes and extents (values 0..10 of both records)
-      bool same = true;
-      for (int i = 0; i < 11; ++i) same = same && a[i] == b[i];
-      if (same) { obj_occ[o] = q; break; }
+      bool on = false;
+      if (kind == MPT_PLANE) {
+        // coplanar: the plane's corner and both far corners lie in b's plane
+        double c1[3], c2[3];
+        for (int j = 0; j < 3; ++j) {
+          c1[j] = a[j] + a[3] * a[4 + j];
+          c2[j] = a[j] + a[7] * a[8 + j];
+        }
+        on = std::fabs(plane_dist(b, a)) < 1e-7 && std::fabs(plane_dist(b, c1)) < 1e-7 &&
+             std::fabs(plane_dist(b, c2)) < 1e-7;
+      } else {
+        double e0[3], e1[3];
+        for (int j = 0; j < 3; ++j) {
+          e0[j] = a[j] + a[3] * a[4 + j];
+          e1[j] = a[j] + a[7] * a[4 + j];
+        }
+        on = std::fabs(plane_dist(b, e0)) < 1e-7 && std::fabs(plane_dist(b, e1)) < 1e-7;
+      }
+      if (on) add_own(q);
     }
   }
   // occluder bounding boxes from FP64 corners, grown by 1 cm: rectangles from
@@ -237,7 +277,7 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   const size_t s_kind = align256((size_t)no * 4), s_o32 = align256((size_t)no * 64),
                s_o64 = align256((size_t)no * 128), s_ck = align256((size_t)nc * 4 + 4),
                s_c32 = align256((size_t)nc * 64 + 16), s_c64 = align256((size_t)nc * 128 + 16),
-               s_oo = align256((size_t)no * 4), s_cb = align256((size_t)nc * 32 + 16),
+               s_oo = align256((size_t)no * 16), s_cb = align256((size_t)nc * 32 + 16),
                s_a32 = align256((size_t)no * 64);
   const size_t total = s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb + s_a32;
   MPT_CUDA_TRY(cudaSetDevice(ctx->device));
@@ -266,7 +306,7 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   d.occ_kind = reinterpret_cast<const int32_t*>(put(nc ? desc->occ_kind : nullptr, (size_t)nc * 4, s_ck));
   d.c32 = reinterpret_cast<const float4*>(put(c32.data(), (size_t)nc * 64, s_c32));
   d.c64 = reinterpret_cast<const double2*>(put(c64.data(), (size_t)nc * 128, s_c64));
-  d.obj_occ = reinterpret_cast<const int32_t*>(put(obj_occ.data(), (size_t)no * 4, s_oo));
+  d.obj_occ = reinterpret_cast<const int4*>(put(obj_occ.data(), (size_t)no * 16, s_oo));
   d.cbox = reinterpret_cast<const float4*>(put(cbox.data(), (size_t)nc * 32, s_cb));
   d.a32 = reinterpret_cast<const float4*>(put(a32.data(), (size_t)no * 64, s_a32));
   d.scale = desc->scale;

@@ -25,7 +25,7 @@ struct DevScene {
   const int32_t* occ_kind;  // [n_occ]
   const float4* c32;        // [4][n_occ]
   const double2* c64;       // [8][n_occ]
-  const int32_t* obj_occ;   // [n_obj]: occluder holding this plane's rectangle, or -1
+  const int4* obj_occ;      // [n_obj]: up to 4 rectangles whose plane holds every point of the object, -1 padded
   const float4* cbox;       // [2][n_occ]: occluder boxes (lo, hi) grown by 1 cm; lo.w = 0 rectangle, 1 paraboloid
   double scale;
 };

@@ -226,12 +226,16 @@ __device__ bool accept_one(const DevScene& sc, const DevEnds& ep, const Cand& cd
 #pragma unroll
   for (int j = 0; j <= N; ++j) {
     const v3<float> Af = P[j], Bf = P[j + 1];
-    // rectangles that hold an end of this segment cannot be crossed strictly
-    const int own0 = j >= 1 ? sc.obj_occ[cd.ids[j - 1]] : -1;
-    const int own1 = j < N ? sc.obj_occ[cd.ids[j]] : -1;
+    // rectangles whose plane holds an end of this segment cannot be crossed
+    // strictly (both ends must be more than EPS_VIS off the plane)
+    const int4 none = make_int4(-1, -1, -1, -1);
+    const int4 own0 = j >= 1 ? sc.obj_occ[cd.ids[j - 1]] : none;
+    const int4 own1 = j < N ? sc.obj_occ[cd.ids[j]] : none;
     for (int o = 0; o < sc.n_occ; ++o) {
-      if (o == own0 || o == own1) continue;
       if (!box_overlap(occ_sm[4 * sc.n_occ + o], occ_sm[5 * sc.n_occ + o], Af, Bf)) continue;
+      if (o == own0.x || o == own0.y || o == own0.z || o == own0.w || o == own1.x || o == own1.y ||
+          o == own1.z || o == own1.w)
+        continue;
       int b = sc.occ_kind[o] == 0 ? rect32(occ_sm, sc.n_occ, o, Af, Bf) : -1;
       if (b < 0)
         b = blocks64(sc, o, point64<N>(sc, ep, cd, Tc, it_, ir_, j), point64<N>(sc, ep, cd, Tc, it_, ir_, j + 1))
