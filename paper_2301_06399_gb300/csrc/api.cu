@@ -279,7 +279,24 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
                s_c32 = align256((size_t)nc * 64 + 16), s_c64 = align256((size_t)nc * 128 + 16),
                s_oo = align256((size_t)no * 16), s_cb = align256((size_t)nc * 32 + 16),
                s_a32 = align256((size_t)no * 64);
-  const size_t total = s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb + s_a32;
+  // boxes of groups of OCC_GROUP consecutive occluders (union of the members'
+  // boxes): a segment that misses a group's box skips its members
+  const int ng = (nc + mpt::OCC_GROUP - 1) / mpt::OCC_GROUP;
+  std::vector<float> gbox((size_t)ng * 8, 0.f);
+  for (int gi = 0; gi < ng; ++gi) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int q = gi * mpt::OCC_GROUP; q < nc && q < (gi + 1) * mpt::OCC_GROUP; ++q)
+      for (int j = 0; j < 3; ++j) {
+        lo[j] = std::fmin(lo[j], cbox[(size_t)4 * q + j]);
+        hi[j] = std::fmax(hi[j], cbox[(size_t)4 * (nc + q) + j]);
+      }
+    for (int j = 0; j < 3; ++j) {
+      gbox[(size_t)4 * gi + j] = lo[j];
+      gbox[(size_t)4 * (ng + gi) + j] = hi[j];
+    }
+  }
+  const size_t s_gb = align256((size_t)ng * 32 + 16);
+  const size_t total = s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb + s_a32 + s_gb;
   MPT_CUDA_TRY(cudaSetDevice(ctx->device));
   void* mem = nullptr;
   MPT_CUDA_TRY(cudaMalloc(&mem, total));
@@ -309,6 +326,8 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   d.obj_occ = reinterpret_cast<const int4*>(put(obj_occ.data(), (size_t)no * 16, s_oo));
   d.cbox = reinterpret_cast<const float4*>(put(cbox.data(), (size_t)nc * 32, s_cb));
   d.a32 = reinterpret_cast<const float4*>(put(a32.data(), (size_t)no * 64, s_a32));
+  d.n_grp = ng;
+  d.gbox = reinterpret_cast<const float4*>(put(gbox.data(), (size_t)ng * 32, s_gb));
   d.scale = desc->scale;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -27,8 +27,12 @@ struct DevScene {
   const double2* c64;       // [8][n_occ]
   const int4* obj_occ;      // [n_obj]: up to 4 rectangles whose plane holds every point of the object, -1 padded
   const float4* cbox;       // [2][n_occ]: occluder boxes (lo, hi) grown by 1 cm; lo.w = 0 rectangle, 1 paraboloid
+  int n_grp;                // ceil(n_occ / OCC_GROUP)
+  const float4* gbox;       // [2][n_grp]: boxes of groups of OCC_GROUP consecutive occluders
   double scale;
 };
+
+constexpr int OCC_GROUP = 4;  // occluders per group box
 
 // A segment can only meet an occluder whose box its own box overlaps (the
 // boxes are grown by 1 cm at upload, far above FP32 rounding of the ends).

@@ -560,7 +560,7 @@ template <int N>
 __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevEnds ep, const float4* ends32,
                                                                CandView cv, SolView out, RefineList rl1,
                                                                RefineList rl2) {
-  extern __shared__ float4 occ_sm[];  // [6][n_occ]
+  extern __shared__ float4 occ_sm[];  // [6][n_occ] records and boxes, then [2][n_grp] group boxes
   int64_t end = cv.order_begin[N];
   if (end > cv.cap) end = cv.cap;
   int64_t begin = cv.order_begin[N - 1];
@@ -568,10 +568,11 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
   int64_t n = (int64_t)rl1.count[N - 1];
   if (n > end - begin) n = end - begin;
   if ((int64_t)blockIdx.x * blockDim.x >= n) return;  // the whole block
-  const int no = sc.n_occ;
-  for (int q = threadIdx.x; q < 6 * no; q += blockDim.x)
-    occ_sm[q] = q < 4 * no ? __ldg(sc.c32 + q) : __ldg(sc.cbox + (q - 4 * no));
+  const int no = sc.n_occ, ng = sc.n_grp;
+  for (int q = threadIdx.x; q < 6 * no + 2 * ng; q += blockDim.x)
+    occ_sm[q] = q < 4 * no ? __ldg(sc.c32 + q) : q < 6 * no ? __ldg(sc.cbox + (q - 4 * no)) : __ldg(sc.gbox + (q - 6 * no));
   __syncthreads();
+  const float4* grp_sm = occ_sm + 6 * no;  // [2][ng]
   const unsigned lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
@@ -603,14 +604,24 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
             hi[j] = mk(fmaxf(P[j].x, P[j + 1].x), fmaxf(P[j].y, P[j + 1].y), fmaxf(P[j].z, P[j + 1].z));
           }
           bool blocked = false;
-          for (int o = 0; o < no && !blocked; ++o) {
-            const float4 bl = occ_sm[4 * no + o], bh = occ_sm[5 * no + o];
-            if (bl.w != 0.f) continue;  // rectangles only
+          for (int gi = 0; gi < ng && !blocked; ++gi) {
+            const float4 gl = grp_sm[gi], gh = grp_sm[ng + gi];
+            bool any = false;
 #pragma unroll
-            for (int j = 0; j <= N; ++j) {
-              if (lo[j].x <= bh.x && hi[j].x >= bl.x && lo[j].y <= bh.y && hi[j].y >= bl.y && lo[j].z <= bh.z &&
-                  hi[j].z >= bl.z)
-                blocked = blocked || clearly_crosses(occ_sm, no, o, P[j], P[j + 1]);
+            for (int j = 0; j <= N; ++j)
+              any = any || (lo[j].x <= gh.x && hi[j].x >= gl.x && lo[j].y <= gh.y && hi[j].y >= gl.y &&
+                            lo[j].z <= gh.z && hi[j].z >= gl.z);
+            if (!any) continue;
+            const int o_end = (gi + 1) * OCC_GROUP < no ? (gi + 1) * OCC_GROUP : no;
+            for (int o = gi * OCC_GROUP; o < o_end && !blocked; ++o) {
+              const float4 bl = occ_sm[4 * no + o], bh = occ_sm[5 * no + o];
+              if (bl.w != 0.f) continue;  // rectangles only
+#pragma unroll
+              for (int j = 0; j <= N; ++j) {
+                if (lo[j].x <= bh.x && hi[j].x >= bl.x && lo[j].y <= bh.y && hi[j].y >= bl.y && lo[j].z <= bh.z &&
+                    hi[j].z >= bl.z)
+                  blocked = blocked || clearly_crosses(occ_sm, no, o, P[j], P[j + 1]);
+              }
             }
           }
           if (blocked) {
@@ -850,7 +861,7 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
 #undef MPT_LAUNCH_GN
   }
   if (PREC == MPT_FP32_FP64REFINE) {
-    const size_t vsmem = (size_t)sc.n_occ * 96;
+    const size_t vsmem = (size_t)sc.n_occ * 96 + (size_t)sc.n_grp * 32;
 #define MPT_LAUNCH_VIS(N)                                                                                   \
   if (vsmem > 48 * 1024)                                                                                    \
     cudaFuncSetAttribute(k_vis_prescreen<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem);      \

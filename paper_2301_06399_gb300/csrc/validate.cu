@@ -231,17 +231,22 @@ __device__ bool accept_one(const DevScene& sc, const DevEnds& ep, const Cand& cd
     const int4 none = make_int4(-1, -1, -1, -1);
     const int4 own0 = j >= 1 ? sc.obj_occ[cd.ids[j - 1]] : none;
     const int4 own1 = j < N ? sc.obj_occ[cd.ids[j]] : none;
-    for (int o = 0; o < sc.n_occ; ++o) {
-      if (!box_overlap(occ_sm[4 * sc.n_occ + o], occ_sm[5 * sc.n_occ + o], Af, Bf)) continue;
-      if (o == own0.x || o == own0.y || o == own0.z || o == own0.w || o == own1.x || o == own1.y ||
-          o == own1.z || o == own1.w)
-        continue;
-      int b = sc.occ_kind[o] == 0 ? rect32(occ_sm, sc.n_occ, o, Af, Bf) : -1;
-      if (b < 0)
-        b = blocks64(sc, o, point64<N>(sc, ep, cd, Tc, it_, ir_, j), point64<N>(sc, ep, cd, Tc, it_, ir_, j + 1))
-                ? 1
-                : 0;
-      if (b) return false;
+    const float4* grp_sm = occ_sm + 6 * sc.n_occ;  // [2][n_grp]
+    for (int gi = 0; gi < sc.n_grp; ++gi) {
+      if (!box_overlap(grp_sm[gi], grp_sm[sc.n_grp + gi], Af, Bf)) continue;
+      const int o_end = (gi + 1) * OCC_GROUP < sc.n_occ ? (gi + 1) * OCC_GROUP : sc.n_occ;
+      for (int o = gi * OCC_GROUP; o < o_end; ++o) {
+        if (!box_overlap(occ_sm[4 * sc.n_occ + o], occ_sm[5 * sc.n_occ + o], Af, Bf)) continue;
+        if (o == own0.x || o == own0.y || o == own0.z || o == own0.w || o == own1.x || o == own1.y ||
+            o == own1.z || o == own1.w)
+          continue;
+        int b = sc.occ_kind[o] == 0 ? rect32(occ_sm, sc.n_occ, o, Af, Bf) : -1;
+        if (b < 0)
+          b = blocks64(sc, o, point64<N>(sc, ep, cd, Tc, it_, ir_, j), point64<N>(sc, ep, cd, Tc, it_, ir_, j + 1))
+                  ? 1
+                  : 0;
+        if (b) return false;
+      }
     }
   }
   return true;
@@ -318,7 +323,8 @@ __device__ bool accept_candidate(const DevScene& sc, const DevEnds& ep, const Ac
   }
 }
 
-// Stages the FP32 occluder records (fields 0-3) and their boxes (fields 4-5)
+// Stages the FP32 occluder records (fields 0-3), their boxes (fields 4-5) and
+// the boxes of groups of OCC_GROUP consecutive occluders (after the fields)
 // into shared memory with bulk copies; every thread waits, bounded, for them.
 // On a wait that gives up, the error flag is set, thread 0 waits (again
 // bounded) for the copy still in flight, and false is returned.
@@ -331,11 +337,13 @@ __device__ bool stage_occluders(const DevScene& sc, float4* occ_sm, uint64_t* ba
   __syncthreads();
   if (sc.n_occ == 0) return true;
   if (threadIdx.x == 0) {
-    mbar_expect_tx(bar, 6u * field_bytes);
+    mbar_expect_tx(bar, 6u * field_bytes + 32u * (uint32_t)sc.n_grp);
 #pragma unroll
     for (int f = 0; f < 4; ++f) bulk_g2s(occ_sm + f * sc.n_occ, sc.c32 + f * sc.n_occ, field_bytes, bar);
 #pragma unroll
     for (int f = 0; f < 2; ++f) bulk_g2s(occ_sm + (4 + f) * sc.n_occ, sc.cbox + f * sc.n_occ, field_bytes, bar);
+    // group boxes: [2][n_grp] right after the six occluder fields
+    bulk_g2s(occ_sm + 6 * sc.n_occ, sc.gbox, 32u * (uint32_t)sc.n_grp, bar);
   }
   bool staged = true;
   unsigned spins = 0;
@@ -581,7 +589,7 @@ static int run_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoint
   const DevEnds ep = dev_ends(ends);
   k_flag<<<(unsigned)n_groups, ACC_BLOCK, 0, st>>>(av, tau, vs);
   MPT_LAUNCH_CHECK();
-  const size_t smem = (size_t)scene->d.n_occ * 96;
+  const size_t smem = (size_t)scene->d.n_occ * 96 + (size_t)scene->d.n_grp * 32;
   if (smem > 48 * 1024) {
     cudaFuncSetAttribute(k_accept_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_accept_ovf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
