@@ -208,6 +208,19 @@ int mpt_scene_free(mpt_scene* scene);
 
 /* ---------------------------------------------------------- candidates */
 
+/* Visibility matrix V of Algorithm 1 (its first line; Sec. III, Fig. 5),
+ * written to vis (device uint8 [n_obj][n_obj], caller-owned), usable as the
+ * adj_mask of mpt_enumerate.  Reading: a planar facet reflects on the side its
+ * normal points to, so V[i][j] = 0 when i == j or when one of the two objects
+ * is a plane and every vertex of the other (rectangle corners, edge ends, the
+ * corners of a paraboloid patch's local box, the corners of the square of
+ * half-side Rc around an arc's centre) lies more than 1e-6 S behind that
+ * plane; otherwise 1.  Edges and paraboloids are seen from every side.  The
+ * test is conservative: it removes only sequences whose planar facets would
+ * have to be used from behind.  Enqueued on `stream`; MPT_ERR_ARG on null
+ * arguments. */
+int mpt_visibility(mpt_ctx* ctx, const mpt_scene* scene, uint8_t* vis, void* stream);
+
 /* Candidate enumeration (Algorithm 1, all_simple_paths over the adjacency
  * matrix of Sec. III / Fig. 5; the BS row and UE column are taken as all
  * ones).  adj_mask: device uint8 [n_obj][n_obj] or NULL (complete graph);

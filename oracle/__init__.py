@@ -253,3 +253,61 @@ def splitmix64(x: int) -> int:
 
 def threads(n: int = 0) -> int:
     return int(lib().oracle_threads(n))
+
+
+# ------------------------------------------------------- visibility matrix --
+def _object_vertices(kind: int, p: np.ndarray) -> np.ndarray:
+    """Points whose convex hull holds every point the object can put on a path
+    (record layouts of include/mpt.h): a rectangle's four corners, a line
+    edge's two ends, the eight corners of the local box [-rho, rho]^2 x
+    [0, rho^2 / (4f)] of a paraboloid patch, the four corners of the square
+    of half-side Rc around an arc's centre in its plane."""
+    if kind == 0:  # plane
+        O, Ua, Va, U, V = p[4:7], p[7:10], p[10:13], p[13], p[14]
+        return np.array([O, O + U * Ua, O + V * Va, O + U * Ua + V * Va])
+    if kind == 2:  # line edge
+        P, e, t0, t1 = p[0:3], p[3:6], p[6], p[7]
+        return np.array([P + t0 * e, P + t1 * e])
+    if kind == 1:  # paraboloid: X = t0 + R (s, t, (s^2 + t^2) / (4 f))
+        R = p[0:9].reshape(3, 3)
+        t0, f, rho = p[9:12], p[12], p[13]
+        out = []
+        for sx in (-rho, rho):
+            for sy in (-rho, rho):
+                for sz in (0.0, rho * rho / (4.0 * f)):
+                    out.append(t0 + R @ np.array([sx, sy, sz]))
+        return np.array(out)
+    # arc edge: X = C + Rc (cos t u + sin t (a x u))
+    C, a, Rc, u = p[0:3], p[3:6], p[6], p[7:10]
+    v = np.cross(a, u)
+    return np.array([C + Rc * (sx * u + sy * v) for sx in (-1.0, 1.0) for sy in (-1.0, 1.0)])
+
+
+def visibility_matrix(scene) -> np.ndarray:
+    """Object visibility matrix V of Algorithm 1 (its first line; Sec. III,
+    Fig. 5), under the reading that a planar facet reflects on the side its
+    normal points to: V[i, j] = 0 when i == j, or when one of the two objects
+    is a plane and every vertex of the other lies more than 1e-6 S behind
+    that plane (<n, X - O> < -1e-6 S); otherwise 1.  Edges and paraboloids
+    are seen from every side.  Used as the adjacency mask of the
+    enumeration.  Plain double loops over the object pairs."""
+    kinds = np.asarray(scene.obj_kind)
+    par = np.asarray(scene.obj_param, np.float64)
+    n = len(kinds)
+    delta = 1e-6 * float(scene.scale)
+    verts = [_object_vertices(int(kinds[i]), par[i]) for i in range(n)]
+
+    def hidden_behind(i: int, j: int) -> bool:
+        # every vertex of object j strictly behind plane i
+        nrm, O = par[i][0:3], par[i][4:7]
+        return all(float(np.dot(nrm, x - O)) < -delta for x in verts[j])
+
+    V = np.ones((n, n), np.uint8)
+    for i in range(n):
+        V[i, i] = 0
+        for j in range(n):
+            if i == j:
+                continue
+            if (kinds[i] == 0 and hidden_behind(i, j)) or (kinds[j] == 0 and hidden_behind(j, i)):
+                V[i, j] = 0
+    return V

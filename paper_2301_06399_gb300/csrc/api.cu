@@ -355,6 +355,11 @@ int64_t mpt_candidate_count(const mpt_scene* scene, const mpt_endpoints* ends, i
   return host_candidate_count(scene, ends, max_order, sampling);
 }
 
+int mpt_visibility(mpt_ctx* ctx, const mpt_scene* scene, uint8_t* vis, void* stream) {
+  if (!ctx || !scene || !vis) return MPT_ERR_ARG;
+  return launch_visibility(ctx, scene, vis, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int mpt_enumerate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, int max_order,
                   const uint8_t* adj_mask, const mpt_sampling* sampling, mpt_candidates* out, void* stream) {
   if (!ctx || !scene || !out || !out->rec || !out->count || !out->order_begin || out->capacity < 0)

@@ -282,4 +282,79 @@ int launch_enumerate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* 
   return over ? MPT_ERR_CAPACITY : MPT_OK;
 }
 
+// ------------------------------------------------------- visibility matrix --
+// V of Algorithm 1 (its first line; Sec. III, Fig. 5) under the reading that
+// a planar facet reflects on the side its normal points to: V[i][j] = 0 when
+// i == j, or when one object is a plane and every vertex of the other lies
+// more than delta behind that plane; otherwise 1.  Vertices bound every
+// point an object can put on a path: a rectangle's corners, a line edge's
+// ends, the corners of a paraboloid patch's local box, the corners of the
+// square of half-side Rc around an arc's centre.  FP64; one thread per pair.
+__device__ int object_vertices(const DevScene& sc, int o, v3<double> (&x)[8]) {
+  const Rec<double> r = load_obj64(sc, o);
+  const int kind = sc.kind[o];
+  if (kind == K_PLANE) {
+    const v3<double> O = r.f3(0), u = r.f3(4), v = r.f3(8);
+    x[0] = O;
+    x[1] = axpy(r.v[3], u, O);
+    x[2] = axpy(r.v[7], v, O);
+    x[3] = axpy(r.v[7], v, x[1]);
+    return 4;
+  }
+  if (kind == K_LINE) {
+    x[0] = axpy(r.v[3], r.f3(4), r.f3(0));
+    x[1] = axpy(r.v[7], r.f3(4), r.f3(0));
+    return 2;
+  }
+  if (kind == K_PARAB) {
+    const v3<double> t0 = mk(r.v[3], r.v[7], r.v[11]);
+    const double rho = r.v[13], h = rho * rho * r.v[12];
+    int m = 0;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        for (int c = 0; c < 2; ++c)
+          x[m++] = axpy(c ? h : 0.0, r.f3(8), axpy(b ? rho : -rho, r.f3(4), axpy(a ? rho : -rho, r.f3(0), t0)));
+    return 8;
+  }
+  const double Rc = r.v[3];
+  int m = 0;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) x[m++] = axpy(b ? Rc : -Rc, r.f3(8), axpy(a ? Rc : -Rc, r.f3(4), r.f3(0)));
+  return 4;
+}
+
+// every vertex of object j more than delta behind plane i
+__device__ bool hidden_behind(const DevScene& sc, int i, int j, double delta) {
+  const Rec<double> p = load_obj64(sc, i);
+  const v3<double> O = p.f3(0), n = p.f3(12);
+  v3<double> x[8];
+  const int m = object_vertices(sc, j, x);
+  for (int k = 0; k < m; ++k)
+    if (!(dot(n, x[k] - O) < -delta)) return false;
+  return true;
+}
+
+__global__ void k_visibility(DevScene sc, double delta, uint8_t* V) {
+  const int64_t n = sc.n_obj;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / n), j = (int)(q % n);
+    uint8_t v = 1;
+    if (i == j) v = 0;
+    else if ((sc.kind[i] == K_PLANE && hidden_behind(sc, i, j, delta)) ||
+             (sc.kind[j] == K_PLANE && hidden_behind(sc, j, i, delta)))
+      v = 0;
+    V[q] = v;
+  }
+}
+
+int launch_visibility(mpt_ctx* ctx, const mpt_scene* scene, uint8_t* vis, cudaStream_t st) {
+  const int64_t pairs = (int64_t)scene->d.n_obj * scene->d.n_obj;
+  int64_t blocks = (pairs + 255) / 256;
+  if (blocks > (int64_t)ctx->sms * 16) blocks = (int64_t)ctx->sms * 16;
+  if (blocks < 1) blocks = 1;
+  k_visibility<<<(unsigned)blocks, 256, 0, st>>>(scene->d, 1e-6 * scene->d.scale, vis);
+  MPT_LAUNCH_CHECK();
+  return MPT_OK;
+}
+
 }  // namespace mpt

@@ -224,6 +224,7 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
                  mpt_solutions* out, cudaStream_t st);
 int launch_enumerate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, int max_order,
                      const uint8_t* adj, const mpt_sampling* smp, mpt_candidates* out, cudaStream_t st);
+int launch_visibility(mpt_ctx* ctx, const mpt_scene* scene, uint8_t* vis, cudaStream_t st);
 int launch_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
                     const mpt_candidates* cand, const mpt_solutions* sol, double tau, mpt_paths* out,
                     int64_t* d_valid_count, cudaStream_t st);

@@ -62,7 +62,7 @@ _lock = threading.Lock()
 # Every symbol include/mpt.h declares.
 SYMBOLS = ["mpt_ctx_create", "mpt_ctx_destroy", "mpt_ctx_sm_count", "mpt_ctx_check", "mpt_scene_upload",
            "mpt_scene_free", "mpt_enumerate", "mpt_candidate_count", "mpt_solve", "mpt_validate", "mpt_grad",
-           "mpt_status_string", "mpt_flop_model", "mpt_validate_noalloc"]
+           "mpt_status_string", "mpt_flop_model", "mpt_validate_noalloc", "mpt_visibility"]
 
 
 def library_path() -> str:
@@ -86,6 +86,7 @@ def lib():
             L.mpt_scene_free.argtypes = [P]
             L.mpt_enumerate.argtypes = [P, P, C.POINTER(Endpoints), C.c_int, P, C.POINTER(Sampling),
                                         C.POINTER(CandStruct), P]
+            L.mpt_visibility.argtypes = [P, P, P, P]
             L.mpt_candidate_count.restype = I64
             L.mpt_candidate_count.argtypes = [P, C.POINTER(Endpoints), C.c_int, C.POINTER(Sampling)]
             L.mpt_solve.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct), C.c_int,
@@ -231,6 +232,15 @@ def alloc_candidates(capacity: int, device, init_seed: int = 0) -> Candidates:
     return Candidates(torch.empty((cap, 4), dtype=torch.int32, device=device),
                       torch.zeros(1, dtype=torch.int64, device=device),
                       torch.zeros(5, dtype=torch.int64, device=device), cap, init_seed)
+
+
+def visibility(ds: DeviceScene, stream=None) -> torch.Tensor:
+    """Visibility matrix V (uint8 [n_obj, n_obj] on the scene's device), usable
+    as the adjacency mask of enumerate_candidates."""
+    n = ds.scene.n_obj
+    V = torch.empty((n, n), dtype=torch.uint8, device=ds.tx.device)
+    _check(lib().mpt_visibility(ds.ctx.h, ds.h, C.c_void_p(V.data_ptr()), _stream(stream)), "mpt_visibility")
+    return V
 
 
 def enumerate_candidates(ds: DeviceScene, max_order: int, spec, adj: torch.Tensor | None = None,

@@ -474,3 +474,46 @@ def test_order_four_full_enumeration_small_scene(mpt, ctx):
     table = oracle.enumerate_sequences(sc, 4, spec)
     assert len(table) == 5 + 20 + 60 + 120
     compare_entries(sc, table, paths, range(len(table)), sc.n_pairs)
+
+
+@pytest.mark.parametrize("name", ["urban_block", "mixed_order", "curved"])
+def test_visibility_matrix_bit_exact(mpt, ctx, name):
+    sc = {"urban_block": lambda: S.urban_block(4), "mixed_order": S.mixed_order_city, "curved": S.curved_scene}[name]()
+    ds = mpt.DeviceScene(ctx, sc)
+    V = mpt.visibility(ds)
+    torch.cuda.synchronize()
+    want = oracle.visibility_matrix(sc)
+    assert np.array_equal(V.cpu().numpy(), want)
+    assert 0 < want.sum() < want.size - len(want)  # the test prunes something
+
+
+def test_visibility_pruning_keeps_every_valid_path_of_the_urban_block(mpt, ctx):
+    # closed boxes: a path that used a wall from behind runs inside a box, so
+    # pruning the enumeration with V loses only paths to receivers that the
+    # workload places inside a footprint (kept there on purpose, validity
+    # decides); every path to a receiver outside the boxes survives
+    sc = S.urban_block(8)
+    spec = S.CONFIG_SPECS["urban_block"]
+    ds, cands, sols, paths = gpu_trace(mpt, ctx, sc, 2, spec)
+    V = mpt.visibility(ds)
+    cm = mpt.enumerate_candidates(ds, 2, spec, adj=V)
+    sm = mpt.solve(ds, cm, mpt.FP32_FP64REFINE)
+    pm = mpt.validate(ds, cm, sm, capacity=cm.capacity)
+    torch.cuda.synchronize()
+    n_full, n_masked = int(cands.count.item()), int(cm.count.item())
+    assert n_masked < 0.75 * n_full
+
+    def keys(c, p):
+        pair, ids, order, start = mpt.decode_candidates(c, int(c.count.item()))
+        sel = p.cand[:p.n()].cpu().numpy()
+        return {(int(pair[k]), tuple(int(x) for x in ids[k][:order[k]])) for k in sel}
+
+    full, masked = keys(cands, paths), keys(cm, pm)
+    assert masked <= full
+
+    def inside(rx):
+        return any(x0 <= rx[0] <= x1 and y0 <= rx[1] <= y1 for (x0, y0, x1, y1, h) in sc.meta["boxes"])
+
+    outside = {k for k in full if not inside(sc.rx[k[0] % sc.rx.shape[0]])}
+    assert len(outside) > 100
+    assert outside <= masked
