@@ -289,6 +289,29 @@ def run_ours(args):
             fp64_ms.append(a.elapsed_time(b))
         n_valid_fp64 = paths.n()
 
+        # ---- the pipeline on the visibility-pruned graph of Algorithm 1
+        # (mpt_visibility as the enumeration's adjacency mask; the masked
+        # enumeration synchronises once to size its table)
+        vis_ms, pr_ms = [], []
+        pr_cands = mpt.alloc_candidates(cands.capacity, dev)
+        for i in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            a, b, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            V = mpt.visibility(ds, stream=stream)
+            b.record(stream)
+            mpt.enumerate_candidates(ds, 2, spec, adj=V, out=pr_cands, stream=stream)
+            mpt.solve(ds, pr_cands, mpt.FP32_FP64REFINE, out=sols, stream=stream)
+            mpt.validate(ds, pr_cands, sols, out=paths, stream=stream)
+            mpt.grad(ds, pr_cands, paths, g_len, g_tx=g_tx, g_rx=g_rx, g_obj=g_obj, stream=stream)
+            c2.record(stream)
+            stream.synchronize()
+            vis_ms.append(a.elapsed_time(b))
+            pr_ms.append(a.elapsed_time(c2))
+        pruned = {"candidates": int(pr_cands.count.item()), "visibility_ms": float(np.median(vis_ms)),
+                  "ms_per_step": float(np.median(pr_ms)), "valid_paths_per_step": paths.n()}
+        pruned["valid_paths_per_sec"] = pruned["valid_paths_per_step"] * ws / (pruned["ms_per_step"] * 1e-3)
+
         # ---- the FP32 minimiser alone (MPT_FP32: endpoint copy + k_gn per
         # order, no prescreen or refinement), for the roofline of the
         # dominant kernel
@@ -376,6 +399,7 @@ def run_ours(args):
                                         "achieved": mini_flops / (float(np.median(mini_ms)) * 1e-3) / 1e12,
                                         "frac": mini_flops / (float(np.median(mini_ms)) * 1e-3) / 1e12 / peak_max},
                      "traffic": profile_traffic("mpt_solve") if args.rx_side == 32 else None},
+        "pruned_graph": pruned,
         "fp64_plain": {"ms_per_step": float(np.median(fp64_ms)),
                        "value": n_cand * ws / (float(np.median(fp64_ms)) * 1e-3), "unit": UNIT,
                        "valid_paths_per_step": n_valid_fp64},
