@@ -114,6 +114,19 @@ int mpt_ctx_create(int device, mpt_ctx** out) {
   cudaMemset(p, 0, 64 * sizeof(unsigned long long) + 256);
   c->counters = reinterpret_cast<unsigned long long*>(p);
   c->err_flag = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(p) + 64 * sizeof(unsigned long long));
+  for (int i = 0; i < 3; ++i) {
+    if (cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaFree(p);
+      delete c;
+      return MPT_ERR_CUDA;
+    }
+  }
+  if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaFree(p);
+    delete c;
+    return MPT_ERR_CUDA;
+  }
   c->vscratch = nullptr;
   c->vscratch_bytes = 0;
   c->rscratch = nullptr;
@@ -132,6 +145,11 @@ int mpt_ctx_destroy(mpt_ctx* ctx) {
   if (ctx->rscratch) cudaFree(ctx->rscratch);
   if (ctx->escratch) cudaFree(ctx->escratch);
   cudaFree(ctx->counters);
+  for (int i = 0; i < 3; ++i) {
+    cudaStreamDestroy(ctx->aux[i]);
+    cudaEventDestroy(ctx->ev_join[i]);
+  }
+  cudaEventDestroy(ctx->ev_fork);
   delete ctx;
   return MPT_OK;
 }

@@ -280,14 +280,18 @@ int launch_grad(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
   const int64_t lim = (int64_t)ctx->sms * 8;
   if (blocks > lim) blocks = lim;
   const DevEnds ep = dev_ends(ends);
-  k_grad<1><<<(unsigned)blocks, GRAD_BLOCK, 0, st>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
-  MPT_LAUNCH_CHECK();
+  // the orders are independent (their sums meet only in atomics): order 2
+  // on the caller's stream, orders 1, 3, 4 on the context's auxiliary streams
+  MPT_CUDA_TRY(fork_streams(ctx, st));
   k_grad<2><<<(unsigned)blocks, GRAD_BLOCK, 0, st>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
   MPT_LAUNCH_CHECK();
-  k_grad<3><<<(unsigned)blocks, GRAD_BLOCK, 0, st>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
+  k_grad<1><<<(unsigned)blocks, GRAD_BLOCK, 0, ctx->aux[0]>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
   MPT_LAUNCH_CHECK();
-  k_grad<4><<<(unsigned)blocks, GRAD_BLOCK, 0, st>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
+  k_grad<3><<<(unsigned)blocks, GRAD_BLOCK, 0, ctx->aux[1]>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
   MPT_LAUNCH_CHECK();
+  k_grad<4><<<(unsigned)blocks, GRAD_BLOCK, 0, ctx->aux[2]>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
+  MPT_LAUNCH_CHECK();
+  MPT_CUDA_TRY(join_streams(ctx, st));
   return MPT_OK;
 }
 

@@ -168,7 +168,27 @@ struct mpt_ctx {
   // FP32 endpoint copies, grown on demand
   void* escratch;
   size_t escratch_bytes;
+  // auxiliary streams for independent per-order chains, and the events that
+  // fork them from and join them back to the caller's stream
+  cudaStream_t aux[3];
+  cudaEvent_t ev_fork, ev_join[3];
 };
+
+// Makes the auxiliary streams wait for the work enqueued on st so far.
+inline cudaError_t fork_streams(mpt_ctx* ctx, cudaStream_t st) {
+  cudaError_t e = cudaEventRecord(ctx->ev_fork, st);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ctx->aux[i], ctx->ev_fork, 0);
+  return e;
+}
+// Makes st wait for the work enqueued on the auxiliary streams.
+inline cudaError_t join_streams(mpt_ctx* ctx, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(ctx->ev_join[i], ctx->aux[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_join[i], 0);
+  }
+  return e;
+}
 
 struct mpt_scene {
   mpt_ctx* ctx;

@@ -840,52 +840,50 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
   // [8..11]: refine list sizes; [12..15]: sizes after the visibility
   // prescreen; [16..19]: fallback queue sizes
   MPT_CUDA_TRY(cudaMemsetAsync(ctx->counters, 0, 20 * sizeof(unsigned long long), st));
+  const size_t vsmem = (size_t)sc.n_occ * 96 + (size_t)sc.n_grp * 32;
+  // the fallback queue reuses the first list's storage (read by then)
+  const RefineList rl3{ctx->counters + 16, rl.idx};
   if (sch && sch->mixed_orders) {
     k_gn_mixed<PREC><<<grid_for(ctx, k_gn_mixed<PREC>, sch), SOLVE_BLOCK, 0, st>>>(sc, ep, ends32, cv, sv, cfg,
                                                                                   ctx->counters + 4, rl);
     MPT_LAUNCH_CHECK();
-  } else {
-    // scenes made of planes and straight edges get the smaller solver
-#define MPT_LAUNCH_GN(N)                                                                                     \
-  if (curved)                                                                                                \
-    k_gn<N, PREC, true><<<grid_for(ctx, k_gn<N, PREC, true>, sch), SOLVE_BLOCK, 0, st>>>(                    \
-        sc, ep, ends32, cv, sv, cfg, ctx->counters + (N - 1), rl);                                           \
-  else                                                                                                       \
-    k_gn<N, PREC, false><<<grid_for(ctx, k_gn<N, PREC, false>, sch), SOLVE_BLOCK, 0, st>>>(                  \
-        sc, ep, ends32, cv, sv, cfg, ctx->counters + (N - 1), rl);                                           \
-  MPT_LAUNCH_CHECK();
-  MPT_LAUNCH_GN(1)
-  MPT_LAUNCH_GN(2)
-  MPT_LAUNCH_GN(3)
-  MPT_LAUNCH_GN(4)
-#undef MPT_LAUNCH_GN
   }
-  if (PREC == MPT_FP32_FP64REFINE) {
-    const size_t vsmem = (size_t)sc.n_occ * 96 + (size_t)sc.n_grp * 32;
-#define MPT_LAUNCH_VIS(N)                                                                                   \
-  if (vsmem > 48 * 1024)                                                                                    \
-    cudaFuncSetAttribute(k_vis_prescreen<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem);      \
-  k_vis_prescreen<N><<<grid_for(ctx, k_vis_prescreen<N>, nullptr, vsmem), SOLVE_BLOCK, vsmem, st>>>(        \
-      sc, ep, ends32, cv, sv, rl, rl2);                                                                     \
-  MPT_LAUNCH_CHECK();
-    MPT_LAUNCH_VIS(1)
-    MPT_LAUNCH_VIS(2)
-    MPT_LAUNCH_VIS(3)
-    MPT_LAUNCH_VIS(4)
-#undef MPT_LAUNCH_VIS
-    // the fallback queue reuses the first list's storage (read by then)
-    const RefineList rl3{ctx->counters + 16, rl.idx};
-#define MPT_LAUNCH_REF(N)                                                                                   \
-  k_refine<N><<<grid_for(ctx, k_refine<N>, nullptr), SOLVE_BLOCK, 0, st>>>(sc, ep, cv, sv, cfg, rl2, rl3); \
-  MPT_LAUNCH_CHECK();                                                                                       \
-  k_refine_fb<N><<<ctx->sms * 4, 32, 0, st>>>(sc, ep, cv, sv, cfg, rl3);                                    \
-  MPT_LAUNCH_CHECK();
-    MPT_LAUNCH_REF(1)
-    MPT_LAUNCH_REF(2)
-    MPT_LAUNCH_REF(3)
-    MPT_LAUNCH_REF(4)
-#undef MPT_LAUNCH_REF
+  // The orders are independent chains (solver, visibility prescreen,
+  // refinement, fallback); order 2 stays on the caller's stream and orders
+  // 1, 3, 4 run on the context's auxiliary streams, joined at the end, so
+  // that the small chains and the tails of each kernel overlap.
+  const bool per_order = !(sch && sch->mixed_orders);
+  MPT_CUDA_TRY(fork_streams(ctx, st));
+#define MPT_CHAIN(N, S)                                                                                        \
+  {                                                                                                            \
+    cudaStream_t s_ = (S);                                                                                     \
+    if (per_order) {                                                                                           \
+      if (curved)                                                                                              \
+        k_gn<N, PREC, true><<<grid_for(ctx, k_gn<N, PREC, true>, sch), SOLVE_BLOCK, 0, s_>>>(                  \
+            sc, ep, ends32, cv, sv, cfg, ctx->counters + (N - 1), rl);                                         \
+      else                                                                                                     \
+        k_gn<N, PREC, false><<<grid_for(ctx, k_gn<N, PREC, false>, sch), SOLVE_BLOCK, 0, s_>>>(                \
+            sc, ep, ends32, cv, sv, cfg, ctx->counters + (N - 1), rl);                                         \
+      MPT_LAUNCH_CHECK();                                                                                      \
+    }                                                                                                          \
+    if (PREC == MPT_FP32_FP64REFINE) {                                                                         \
+      if (vsmem > 48 * 1024)                                                                                   \
+        cudaFuncSetAttribute(k_vis_prescreen<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem);     \
+      k_vis_prescreen<N><<<grid_for(ctx, k_vis_prescreen<N>, nullptr, vsmem), SOLVE_BLOCK, vsmem, s_>>>(       \
+          sc, ep, ends32, cv, sv, rl, rl2);                                                                    \
+      MPT_LAUNCH_CHECK();                                                                                      \
+      k_refine<N><<<grid_for(ctx, k_refine<N>, nullptr), SOLVE_BLOCK, 0, s_>>>(sc, ep, cv, sv, cfg, rl2, rl3); \
+      MPT_LAUNCH_CHECK();                                                                                      \
+      k_refine_fb<N><<<ctx->sms * 4, 32, 0, s_>>>(sc, ep, cv, sv, cfg, rl3);                                   \
+      MPT_LAUNCH_CHECK();                                                                                      \
+    }                                                                                                          \
   }
+  MPT_CHAIN(2, st)
+  MPT_CHAIN(1, ctx->aux[0])
+  MPT_CHAIN(3, ctx->aux[1])
+  MPT_CHAIN(4, ctx->aux[2])
+#undef MPT_CHAIN
+  MPT_CUDA_TRY(join_streams(ctx, st));
   return MPT_OK;
 }
 
