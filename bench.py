@@ -289,6 +289,20 @@ def run_ours(args):
             fp64_ms.append(a.elapsed_time(b))
         n_valid_fp64 = paths.n()
 
+        # ---- received field of the valid paths (Sec. V; 1 GHz, PEC
+        # reflections, unit diffraction coefficient), on the last step's paths
+        fld = torch.zeros((ds.n_pairs, 2), dtype=torch.float64, device=dev)
+        field_ms = []
+        for i in range(max(3, min(args.steps, 10))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mpt.field(ds, cands, paths, 2 * np.pi / 0.3, 1.0, -1.0, 1.0, out=fld, stream=stream)
+            b.record(stream)
+            stream.synchronize()
+            field_ms.append(a.elapsed_time(b))
+        field_leg = {"ms": float(np.median(field_ms)), "paths": paths.n(),
+                     "paths_per_sec": paths.n() / (float(np.median(field_ms)) * 1e-3)}
+
         # ---- the pipeline on the visibility-pruned graph of Algorithm 1
         # (mpt_visibility as the enumeration's adjacency mask; the masked
         # enumeration synchronises once to size its table)
@@ -400,6 +414,7 @@ def run_ours(args):
                                         "frac": mini_flops / (float(np.median(mini_ms)) * 1e-3) / 1e12 / peak_max},
                      "traffic": profile_traffic("mpt_solve") if args.rx_side == 32 else None},
         "pruned_graph": pruned,
+        "field": field_leg,
         "fp64_plain": {"ms_per_step": float(np.median(fp64_ms)),
                        "value": n_cand * ws / (float(np.median(fp64_ms)) * 1e-3), "unit": UNIT,
                        "valid_paths_per_step": n_valid_fp64},

@@ -311,6 +311,33 @@ int mpt_grad(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
              const double* g_len, const double* g_pts, double* g_tx, double* g_rx, double* g_obj,
              void* stream);
 
+/* ---------------------------------------------------------------- field */
+
+/* Parameters of mpt_field: wavenumber k = 2 pi / lambda (1/m), the source's
+ * field magnitude E0 at 1 m, and one complex coefficient (re, im) for every
+ * reflection and one for every diffraction (the paper's dyadic coefficients
+ * are not given there; a perfect conductor reflects with (-1, 0) in the
+ * scalar, perpendicular-polarisation form). */
+typedef struct {
+  double wavenumber;
+  double e0;
+  double refl[2];
+  double diff[2];
+} mpt_field_params;
+
+/* Received field (Sec. V, Eqs. 16-19) of the first min(*d_valid_count,
+ * paths->capacity) paths, scalar form: a path with segment lengths d_0..d_n
+ * (TX to the first point, ..., last point to RX) and total length L
+ * contributes E0 e^{-jkL} / d_0 times, for interaction k with r_k = d_0 + ...
+ * + d_{k-1}, refl * r_k / (r_k + d_k) (reflection, Eq. 17) or
+ * diff * sqrt(r_k / (d_k (r_k + d_k))) (diffraction, Eq. 18); contributions
+ * are added (+=, atomically) into field, device double [n_pairs][2] (re, im)
+ * indexed by the candidate's TX/RX pair (Eq. 19).  MPT_ERR_ARG on null
+ * arguments or a non-positive wavenumber. */
+int mpt_field(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
+              const mpt_candidates* cand, const mpt_paths* paths, const int64_t* d_valid_count,
+              const mpt_field_params* params, double* field, void* stream);
+
 /* --------------------------------------------------------------- misc */
 
 const char* mpt_status_string(int status);

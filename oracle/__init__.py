@@ -311,3 +311,40 @@ def visibility_matrix(scene) -> np.ndarray:
             if (kinds[i] == 0 and hidden_behind(i, j)) or (kinds[j] == 0 and hidden_behind(j, i)):
                 V[i, j] = 0
     return V
+
+
+# -------------------------------------------------------------- path field --
+def path_field(scene, table: SequenceTable, sol: Solutions, ver: Verdicts, wavenumber: float, e0: float = 1.0,
+               refl: complex = -1.0, diff: complex = 1.0) -> np.ndarray:
+    """Received field per TX/RX pair (Sec. V, Eqs. 16-19), scalar form: every
+    valid path with segment lengths d_0..d_n (total L) adds
+    E0 e^{-jkL} / d_0 * prod_k C_k, where interaction k, reached after
+    r_k = d_0 + ... + d_{k-1}, has C = refl * r_k / (r_k + d_k) (reflection,
+    Eq. 17) or C = diff * sqrt(r_k / (d_k (r_k + d_k))) (diffraction, Eq.
+    18).  Returns complex128 [n_pairs].  Plain loops over the valid paths."""
+    n_pairs = scene.n_pairs
+    out = np.zeros(n_pairs, np.complex128)
+    kinds = np.asarray(scene.obj_kind)
+    tx, rx = np.asarray(scene.tx), np.asarray(scene.rx)
+    for i in np.nonzero(ver.valid)[0]:
+        c = sol.begin + int(i)
+        e, p = divmod(c, n_pairs)
+        n = int(table.order[e])
+        ids = table.ids[e][:n]
+        if scene.pair_mode == 0:
+            a, b = tx[p // len(rx)], rx[p % len(rx)]
+        else:
+            a, b = tx[p], rx[p]
+        pts = [a] + [sol.X[i, 3 * k:3 * k + 3] for k in range(n)] + [b]
+        d = [float(np.linalg.norm(pts[k + 1] - pts[k])) for k in range(n + 1)]
+        amp = complex(e0) / d[0]
+        r = d[0]
+        for k in range(n):
+            s = d[k + 1]
+            if kinds[ids[k]] in (2, 3):
+                amp *= diff * np.sqrt(r / (s * (r + s)))
+            else:
+                amp *= refl * r / (r + s)
+            r += s
+        out[p] += amp * np.exp(-1j * wavenumber * sum(d))
+    return out

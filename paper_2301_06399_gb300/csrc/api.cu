@@ -423,4 +423,15 @@ int mpt_grad(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, co
                      reinterpret_cast<cudaStream_t>(stream));
 }
 
+int mpt_field(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
+              const mpt_paths* paths, const int64_t* d_valid_count, const mpt_field_params* params, double* field,
+              void* stream) {
+  if (!ctx || !scene || !cand || !paths || !d_valid_count || !params || !field || !cand->rec || !paths->cand ||
+      !paths->X || !(params->wavenumber > 0))
+    return MPT_ERR_ARG;
+  if (check_ends(ends) != MPT_OK) return MPT_ERR_ARG;
+  return launch_field(ctx, scene, ends, cand, paths, d_valid_count, params, field,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"

@@ -245,6 +245,9 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
 int launch_enumerate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, int max_order,
                      const uint8_t* adj, const mpt_sampling* smp, mpt_candidates* out, cudaStream_t st);
 int launch_visibility(mpt_ctx* ctx, const mpt_scene* scene, uint8_t* vis, cudaStream_t st);
+int launch_field(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
+                 const mpt_paths* paths, const int64_t* d_valid_count, const mpt_field_params* fp, double* field,
+                 cudaStream_t st);
 int launch_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
                     const mpt_candidates* cand, const mpt_solutions* sol, double tau, mpt_paths* out,
                     int64_t* d_valid_count, cudaStream_t st);

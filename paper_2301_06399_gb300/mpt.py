@@ -31,6 +31,10 @@ class SceneDesc(C.Structure):
                 ("occ_param", P), ("scale", D)]
 
 
+class FieldParams(C.Structure):
+    _fields_ = [("wavenumber", D), ("e0", D), ("refl", D * 2), ("diff", D * 2)]
+
+
 class Endpoints(C.Structure):
     _fields_ = [("tx", P), ("n_tx", I32), ("rx", P), ("n_rx", I32), ("pair_mode", I32)]
 
@@ -62,7 +66,7 @@ _lock = threading.Lock()
 # Every symbol include/mpt.h declares.
 SYMBOLS = ["mpt_ctx_create", "mpt_ctx_destroy", "mpt_ctx_sm_count", "mpt_ctx_check", "mpt_scene_upload",
            "mpt_scene_free", "mpt_enumerate", "mpt_candidate_count", "mpt_solve", "mpt_validate", "mpt_grad",
-           "mpt_status_string", "mpt_flop_model", "mpt_validate_noalloc", "mpt_visibility"]
+           "mpt_status_string", "mpt_flop_model", "mpt_validate_noalloc", "mpt_visibility", "mpt_field"]
 
 
 def library_path() -> str:
@@ -87,6 +91,8 @@ def lib():
             L.mpt_enumerate.argtypes = [P, P, C.POINTER(Endpoints), C.c_int, P, C.POINTER(Sampling),
                                         C.POINTER(CandStruct), P]
             L.mpt_visibility.argtypes = [P, P, P, P]
+            L.mpt_field.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct), C.POINTER(PathStruct), P,
+                                    C.POINTER(FieldParams), P, P]
             L.mpt_candidate_count.restype = I64
             L.mpt_candidate_count.argtypes = [P, C.POINTER(Endpoints), C.c_int, C.POINTER(Sampling)]
             L.mpt_solve.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct), C.c_int,
@@ -342,6 +348,21 @@ def validate(ds: DeviceScene, cands: Candidates, sols: Solutions, tau: float = T
     ps = out.struct()
     _check(lib().mpt_validate(ds.ctx.h, ds.h, C.byref(ep), C.byref(cs), C.byref(ss), tau, C.byref(ps),
                               _ptr(out.count), _stream(stream)), "mpt_validate")
+    return out
+
+
+def field(ds: DeviceScene, cands: Candidates, paths: Paths, wavenumber: float, e0: float = 1.0,
+          refl: complex = -1.0, diff: complex = 1.0, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Received field per TX/RX pair (float64 [n_pairs, 2] = re, im), added into `out`."""
+    if out is None:
+        out = torch.zeros((ds.n_pairs, 2), dtype=torch.float64, device=ds.tx.device)
+    fp = FieldParams(float(wavenumber), float(e0), (D * 2)(complex(refl).real, complex(refl).imag),
+                     (D * 2)(complex(diff).real, complex(diff).imag))
+    ep = ds.endpoints()
+    cs = cands.struct()
+    ps = paths.struct()
+    _check(lib().mpt_field(ds.ctx.h, ds.h, C.byref(ep), C.byref(cs), C.byref(ps), C.c_void_p(paths.count.data_ptr()),
+                           C.byref(fp), C.c_void_p(out.data_ptr()), _stream(stream)), "mpt_field")
     return out
 
 

@@ -517,3 +517,23 @@ def test_visibility_pruning_keeps_every_valid_path_of_the_urban_block(mpt, ctx):
     outside = {k for k in full if not inside(sc.rx[k[0] % sc.rx.shape[0]])}
     assert len(outside) > 100
     assert outside <= masked
+
+
+def test_received_field_matches_oracle(mpt, ctx):
+    # Sec. V, Eqs. 16-19 at 1 GHz; points agree to 1e-6 m, so each path's
+    # phase to k * 3e-6 rad: the bound below is that, summed over the paths
+    sc = S.urban_block(4)
+    spec = S.CONFIG_SPECS["urban_block"]
+    ds, cands, sols, paths = gpu_trace(mpt, ctx, sc, 2, spec)
+    k = 2 * np.pi / 0.3
+    refl, diff = -1.0, 0.25 - 0.1j
+    got = mpt.field(ds, cands, paths, k, 1.0, refl, diff)
+    torch.cuda.synchronize()
+    got = got[:, 0].cpu().numpy() + 1j * got[:, 1].cpu().numpy()
+    table = oracle.enumerate_sequences(sc, 2, spec)
+    sol, ver = oracle.candidate_range(sc, table, 0, len(table) * sc.n_pairs)
+    assert not ver.ambiguous[ver.valid > 0].any()
+    want = oracle.path_field(sc, table, sol, ver, k, 1.0, refl, diff)
+    mag = oracle.path_field(sc, table, sol, ver, 0.0 + 1e-300, 1.0, abs(refl), abs(diff))  # sum of |contributions|
+    assert np.all(np.abs(got - want) <= 2 * k * 3e-6 * np.abs(mag) + 1e-15)
+    assert np.abs(want).max() > 0
