@@ -325,10 +325,13 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   s->n_obj = no;
   s->host_kind = reinterpret_cast<int32_t*>(std::malloc(sizeof(int32_t) * no));
   std::memcpy(s->host_kind, desc->obj_kind, sizeof(int32_t) * no);
+  // every array is laid out in one host image of the allocation and sent
+  // with a single copy (one transfer instead of one per array)
+  std::vector<unsigned char> image(total, 0);
   size_t off = 0;
   auto put = [&](const void* src, size_t n, size_t span) -> void* {
     void* dst = b + off;
-    if (n) cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
+    if (n) std::memcpy(image.data() + off, src, n);
     off += span;
     return dst;
   };
@@ -347,7 +350,8 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   d.n_grp = ng;
   d.gbox = reinterpret_cast<const float4*>(put(gbox.data(), (size_t)ng * 32, s_gb));
   d.scale = desc->scale;
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaMemcpy(mem, image.data(), total, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     cudaFree(mem);
     std::free(s->host_kind);
