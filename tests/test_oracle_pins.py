@@ -304,6 +304,161 @@ def test_fermat_grid_single_reflection_and_two_edges():
     assert np.linalg.norm(sol.X[0, 3:6] - (P1 + best[2] * d1)) < 1e-5
 
 
+# ------------------------------------------- curved order-1 completeness --
+def _paraboloid_stationary_points(R, t0, f, rho, A, B, n=40):
+    """Every stationary point of L(s, t) = |X - A| + |B - X| over the disc of
+    z = (s^2 + t^2) / (4 f) (Fermat: the reflection points are among them),
+    by damped Newton on the gradient of L from a dense grid of starts; the
+    Hessian by central differences of the gradient."""
+    g = np.linspace(-rho, rho, n)
+    U = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2)
+    U = U[(U ** 2).sum(1) <= (1.05 * rho) ** 2]
+
+    def grad(U):
+        s, t = U[:, 0], U[:, 1]
+        X = np.stack([s, t, (s * s + t * t) / (4 * f)], 1) @ R.T + t0
+        d, e = X - A, B - X
+        w = d / np.linalg.norm(d, axis=1, keepdims=True) - e / np.linalg.norm(e, axis=1, keepdims=True)
+        dx = np.stack([np.ones_like(s), np.zeros_like(s), s / (2 * f)], 1) @ R.T
+        dy = np.stack([np.zeros_like(s), np.ones_like(s), t / (2 * f)], 1) @ R.T
+        return np.stack([(w * dx).sum(1), (w * dy).sum(1)], 1)
+
+    h = 1e-7
+    for _ in range(60):
+        G = grad(U)
+        H = np.stack([(grad(U + [h, 0]) - grad(U - [h, 0])) / (2 * h),
+                      (grad(U + [0, h]) - grad(U - [0, h])) / (2 * h)], 2)
+        det = H[:, 0, 0] * H[:, 1, 1] - H[:, 0, 1] * H[:, 1, 0]
+        ok = np.abs(det) > 1e-14
+        step = np.zeros_like(U)
+        step[ok, 0] = (H[ok, 1, 1] * G[ok, 0] - H[ok, 0, 1] * G[ok, 1]) / det[ok]
+        step[ok, 1] = (-H[ok, 1, 0] * G[ok, 0] + H[ok, 0, 0] * G[ok, 1]) / det[ok]
+        nrm = np.linalg.norm(step, axis=1, keepdims=True)
+        U = np.clip(U - step * np.minimum(1.0, 0.5 * rho / np.maximum(nrm, 1e-300)), -3 * rho, 3 * rho)
+    U = U[np.linalg.norm(grad(U), axis=1) < 1e-11]
+    out = []
+    for u in U:
+        if not any(np.linalg.norm(u - q) < 1e-7 for q in out):
+            out.append(u)
+    return out
+
+
+def _distinct(points, tol=1e-6):
+    out = []
+    for x in points:
+        if not any(np.linalg.norm(x - q) < tol for q in out):
+            out.append(np.array(x))
+    return out
+
+
+def _same_sets(a, b, tol=1e-6):
+    missed = [x for x in a if not any(np.linalg.norm(x - q) < tol for q in b)]
+    extra = [x for x in b if not any(np.linalg.norm(x - q) < tol for q in a)]
+    return missed, extra
+
+
+def test_paraboloid_order1_root_set_matches_dense_scan():
+    """Order-1 completeness on a paraboloid (Sec. III-B, multi-start guesses
+    of Algorithm 1): in deep bowls with both ends inside, where a sequence
+    has up to three reflection points, the valid solutions over 64 starts are
+    exactly the mirror-law stationary points of the path length found by a
+    dense Newton scan of the disc; with the 8 starts of the workloads they
+    are a subset (no false roots).  Points within 1 mm of the rim are left
+    out on both sides (the bounds band)."""
+    rng = np.random.default_rng(1)
+    rho, n_multi = 2.0, 0
+    totals = {8: 0, 64: 0}
+    n_roots = 0
+    for _ in range(40):
+        R = S._random_rotation(rng)
+        t0 = rng.uniform(-3, 3, 3)
+        f = rng.uniform(0.5, 1.2)
+        A = t0 + R @ np.array([*rng.uniform(-1.5, 1.5, 2), rng.uniform(0.2, 2.0)])
+        B = t0 + R @ np.array([*rng.uniform(-1.5, 1.5, 2), rng.uniform(0.2, 2.0)])
+        P = lambda u: t0 + R @ np.array([u[0], u[1], (u[0] ** 2 + u[1] ** 2) / (4 * f)])
+        roots = []
+        for u in _paraboloid_stationary_points(R, t0, f, rho, A, B):
+            if math.hypot(*u) > rho - 1e-3:
+                continue
+            x = P(u)
+            i = (x - A) / np.linalg.norm(x - A)
+            r = (B - x) / np.linalg.norm(B - x)
+            nm = R @ np.array([u[0] / (2 * f), u[1] / (2 * f), -1.0])
+            nm /= np.linalg.norm(nm)
+            if np.linalg.norm(r - (i - 2 * np.dot(i, nm) * nm)) < 1e-8:  # a reflection, not a crossing
+                roots.append(x)
+        n_roots += len(roots)
+        n_multi += len(roots) > 1
+        b = _builder()
+        b.paraboloid(R, t0, f, rho, occluder=False)
+        sc = b.build("bowl", 100.0, A[None], B[None], pair_mode=1)
+        for starts in (8, 64):
+            table = oracle.enumerate_sequences(sc, 1, S.SequenceSpec(quota=(-1, 0, 0, 0), starts_curved=starts))
+            sol, ver = oracle.candidate_range(sc, table, 0, len(table))
+            found = []
+            for c in range(len(table)):
+                loc = R.T @ (sol.X[c, :3] - t0)
+                if ver.valid[c] and math.hypot(loc[0], loc[1]) < rho - 1e-3:
+                    found.append(sol.X[c, :3])
+            missed, extra = _same_sets(roots, _distinct(found))
+            assert not extra, "a valid solution that is not a reflection point"
+            if starts == 64:
+                assert not missed
+            totals[starts] += len(roots) - len(missed)
+    assert n_multi >= 3 and n_roots >= 30
+    print(f"paraboloid order 1: {n_roots} roots; found with 8 starts {totals[8]}, with 64 starts {totals[64]}")
+
+
+def test_arc_diffraction_order1_root_set_matches_1d_scan():
+    """Order-1 completeness on an arc edge (Eq. 9 on Eq. 4's curve): the
+    diffraction points are the zeros of dL/dphi along the arc; a 4000-sample
+    sign scan with bisection finds them all, and the valid solutions over the
+    8 starts of the workloads are exactly that set.  Points within 1 mm (arc
+    length) of an end are left out on both sides."""
+    from scipy.optimize import brentq
+
+    rng = np.random.default_rng(2)
+    n_roots = n_multi = 0
+    for _ in range(60):
+        R = S._random_rotation(rng)
+        C = rng.uniform(-2, 2, 3)
+        Rc = rng.uniform(1, 4)
+        a, u = R[:, 2], R[:, 0]
+        v = np.cross(a, u)
+        phi0 = rng.uniform(-math.pi, math.pi)
+        phi1 = phi0 + rng.uniform(math.pi / 4, math.pi)
+        A = C + rng.uniform(-6, 6, 3)
+        B = C + rng.uniform(-6, 6, 3)
+        X = lambda p: C + Rc * (math.cos(p) * u + math.sin(p) * v)
+
+        def dL(p):
+            x = X(p)
+            w = (x - A) / np.linalg.norm(x - A) - (B - x) / np.linalg.norm(B - x)
+            return float(np.dot(w, Rc * (-math.sin(p) * u + math.cos(p) * v)))
+
+        ph = np.linspace(phi0, phi1, 4001)
+        d = np.array([dL(p) for p in ph])
+        band = 1e-3 / Rc
+        roots = [X(p) for p in (brentq(dL, ph[k], ph[k + 1], xtol=1e-15) for k in range(len(ph) - 1)
+                                if d[k] * d[k + 1] < 0) if phi0 + band < p < phi1 - band]
+        n_roots += len(roots)
+        n_multi += len(roots) > 1
+        b = _builder()
+        b.arc_edge(C, a, Rc, u, phi0, phi1)
+        sc = b.build("arc", 100.0, A[None], B[None], pair_mode=1)
+        table = oracle.enumerate_sequences(sc, 1, S.SequenceSpec(quota=(-1, 0, 0, 0), starts_curved=8))
+        sol, ver = oracle.candidate_range(sc, table, 0, len(table))
+        found = []
+        for c in range(len(table)):
+            ang = phi0 + math.fmod(sol.T[c, 0] - phi0, 2 * math.pi)
+            ang += 2 * math.pi if ang < phi0 else 0.0
+            if ver.valid[c] and phi0 + band < ang < phi1 - band:
+                found.append(sol.X[c, :3])
+        missed, extra = _same_sets(roots, _distinct(found))
+        assert not missed and not extra
+    assert n_multi >= 3 and n_roots >= 40
+
+
 # ---------------------------------------------------- invariances ---------
 def test_solution_invariant_to_normal_and_edge_direction_signs():
     sc = S.urban_block(4)
