@@ -333,6 +333,47 @@ def test_curved_geometry_sampled(mpt, ctx):
     assert total == 0 or agree >= 0.95 * total
 
 
+def test_deep_bowl_root_sets(mpt, ctx):
+    """Order-1 reflections in deep paraboloid bowls with both ends inside
+    (up to three reflection points per sequence): with 64 starts the GPU's
+    distinct valid roots equal the oracle's (which the oracle pins equate to
+    a dense scan of the path-length stationary points); with 8 starts every
+    GPU root is one of them."""
+    rng = np.random.default_rng(1)
+    rho = 2.0
+    n_roots = 0
+    for _ in range(40):
+        R = S._random_rotation(rng)
+        t0 = rng.uniform(-3, 3, 3)
+        f = rng.uniform(0.5, 1.2)
+        A = t0 + R @ np.array([*rng.uniform(-1.5, 1.5, 2), rng.uniform(0.2, 2.0)])
+        B = t0 + R @ np.array([*rng.uniform(-1.5, 1.5, 2), rng.uniform(0.2, 2.0)])
+        b = S._Builder()
+        b.paraboloid(R, t0, f, rho, occluder=False)
+        sc = b.build("bowl", 100.0, A[None], B[None], pair_mode=1)
+
+        def inside(x):
+            loc = R.T @ (x - t0)
+            return np.hypot(loc[0], loc[1]) < rho - 1e-3
+
+        roots = {}
+        for starts in (64, 8):
+            spec = S.SequenceSpec(quota=(-1, 0, 0, 0), starts_curved=starts)
+            _, _, _, paths = gpu_trace(mpt, ctx, sc, 1, spec)
+            n = paths.n()
+            gX = [x for x in paths.X[:3, :n].cpu().numpy().T if inside(x)]
+            table = oracle.enumerate_sequences(sc, 1, spec)
+            sol, ver = oracle.candidate_range(sc, table, 0, len(table))
+            oX = [sol.X[c, :3] for c in range(len(table)) if ver.valid[c] and inside(sol.X[c, :3])]
+            roots[starts] = (_root_sets(gX, 1e-6), _root_sets(oX, 1e-6))
+        g64, o64 = roots[64]
+        assert len(g64) == len(o64) and all(any(np.abs(x - y).max() < 1e-6 for y in o64) for x in g64)
+        g8, _ = roots[8]
+        assert all(any(np.abs(x - y).max() < 1e-6 for y in o64) for x in g8)
+        n_roots += len(o64)
+    assert n_roots >= 30
+
+
 # --------------------------------------------------------------- adjoint --
 def _oracle_grad_sums(sc, table, paths_cand, paths_T, g_len, g_pts):
     gtx = np.zeros_like(sc.tx)
