@@ -394,7 +394,8 @@ def run_ours(args):
             mpt.grad(ds_e, cands, paths, g_len, g_tx=g_tx, g_rx=g_rx, g_obj=g_obj, stream=stream)
             nv = min(int(paths.count.item()), path_cap)  # device -> host count
             out_cand[:nv].copy_(paths.cand[:nv], non_blocking=True)
-            out_X[:, :nv].copy_(paths.X[:, :nv], non_blocking=True)
+            for r in range(12):  # one contiguous copy per coordinate row
+                out_X[r, :nv].copy_(paths.X[r, :nv], non_blocking=True)
             out_len[:nv].copy_(paths.length[:nv], non_blocking=True)
             out_gtx.copy_(g_tx, non_blocking=True)
             stream.synchronize()

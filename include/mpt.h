@@ -305,7 +305,11 @@ int mpt_ctx_check(mpt_ctx* ctx, void* stream);
  *   g_rx  device double [n_rx][3]   d/d RX position
  *   g_obj device double [n_obj]     d/d offset d of each plane <n, X> = d
  *                                   (moved along n; other kinds get 0)
- * Any of g_tx, g_rx, g_obj may be NULL. */
+ * Any of g_tx, g_rx, g_obj may be NULL.  With g_pts NULL the length is
+ * stationary at every path (Fermat: the laws of Eqs. 8-9), so its gradient
+ * is the explicit one (envelope theorem: -u_0 for TX, u_n for RX,
+ * <u_m - u_m+1, n> for a plane offset, u_j the unit segment directions) and
+ * no linear system is solved. */
 int mpt_grad(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
              const mpt_candidates* cand, const mpt_paths* paths, const int64_t* d_valid_count,
              const double* g_len, const double* g_pts, double* g_tx, double* g_rx, double* g_obj,

@@ -4,6 +4,8 @@
 //   v = gL dL/dT + gX dX/dT,   lambda = (J^T J)^{-1} v,   z = J lambda,
 // the vector-Jacobian product is
 //   dtheta += gL dL/dtheta|explicit + gX dX/dtheta|explicit - z^T drho/dtheta.
+// Without point weights (gX = 0) v vanishes at a solution and only the
+// explicit term is left, which needs no linear solve.
 // theta: TX (a fixed point before interaction 1), RX (after interaction n)
 // and the offset d of each plane <n, X> = d (its points move along n).
 // One thread per valid path, in float-float (about 48 significand bits).
@@ -69,14 +71,6 @@ __device__ bool grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, 
     prm[2 * k] = ff_from_double(Tc[2 * k]);
     prm[2 * k + 1] = ff_from_double(Tc[2 * k + 1]);
   }
-  // normal matrix at the solution
-  S jtj[Q * (Q + 1) / 2], g[Q];
-  bool ok;
-  eval_path<N, S, S, true>(kind, rec, prm, A, B, jtj, g, ok);
-#pragma unroll
-  for (int k = 0; k < N; ++k)
-    if (is_edge(kind[k])) jtj[tri(2 * k + 1, 2 * k + 1)] = S(1);
-  if (!cholesky<Q, S>(jtj, S(0))) return false;
   // geometry
   PointT<S> pt[N];
 #pragma unroll
@@ -91,6 +85,39 @@ __device__ bool grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, 
     il[j] = rsq(dot(d, d));
     u[j] = d * il[j];
   }
+  o.it = it_;
+  o.ir = ir_;
+  if (gX == nullptr) {
+    // Length weights only.  A path obeys the laws of Eqs. 8-9 exactly when
+    // its length is stationary in the parameters (Fermat), so dL/dT = 0,
+    // v = 0, lambda = 0 and the gradient is the explicit one (envelope
+    // theorem): dL/dTX = -u_0, dL/dRX = u_n, dL/dd = <u_m - u_m+1, n> for a
+    // reflection on the plane <n, X> = d.  No normal matrix is needed.
+    if (want_tx) {
+      o.tx[0] = to_double(-gLs * u[0].x);
+      o.tx[1] = to_double(-gLs * u[0].y);
+      o.tx[2] = to_double(-gLs * u[0].z);
+    }
+    if (want_rx) {
+      o.rx[0] = to_double(gLs * u[N].x);
+      o.rx[1] = to_double(gLs * u[N].y);
+      o.rx[2] = to_double(gLs * u[N].z);
+    }
+    if (want_obj) {
+#pragma unroll
+      for (int m = 0; m < N; ++m)
+        o.obj[m] = kind[m] == K_PLANE ? to_double(gLs * dot(u[m] - u[m + 1], rec[m].f3(12))) : 0.0;
+    }
+    return true;
+  }
+  // normal matrix at the solution
+  S jtj[Q * (Q + 1) / 2], g[Q];
+  bool ok;
+  eval_path<N, S, S, true>(kind, rec, prm, A, B, jtj, g, ok);
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if (is_edge(kind[k])) jtj[tri(2 * k + 1, 2 * k + 1)] = S(1);
+  if (!cholesky<Q, S>(jtj, S(0))) return false;
   Inter in[N];
   S curv_c[N];
   S inv_nn[N];
@@ -154,8 +181,6 @@ __device__ bool grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, 
     }
     z[k] = r;
   }
-  o.it = it_;
-  o.ir = ir_;
   // TX: a displacement of X_0 enters interaction 0 as "previous point"
   if (want_tx) {
     const v3<S> ex = mk(S(1), S(0), S(0)), ey = mk(S(0), S(1), S(0)), ez = mk(S(0), S(0), S(1));

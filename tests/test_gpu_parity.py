@@ -399,8 +399,12 @@ def _oracle_grad_sums(sc, table, paths_cand, paths_T, g_len, g_pts):
     return gtx, grx, gobj
 
 
+@pytest.mark.parametrize("with_pts", [True, False])
 @pytest.mark.parametrize("name", ["street_canyon", "urban4"])
-def test_adjoint_matches_oracle_gradient(mpt, ctx, name):
+def test_adjoint_matches_oracle_gradient(mpt, ctx, name, with_pts):
+    """Full adjoint (length and point weights: the normal-matrix solve), and
+    length weights alone (the explicit-gradient path of the library),
+    against the oracle's implicit-function-theorem gradient."""
     sc = S.street_canyon() if name == "street_canyon" else S.urban_block(4)
     spec = S.CONFIG_SPECS["street_canyon"]
     ds, cands, sols, paths = gpu_trace(mpt, ctx, sc, 2, spec)
@@ -408,7 +412,9 @@ def test_adjoint_matches_oracle_gradient(mpt, ctx, name):
     rng = np.random.default_rng(4)
     g_len = torch.as_tensor(rng.uniform(0.5, 1.5, paths.capacity)).cuda()
     g_pts = torch.as_tensor(rng.normal(size=(12, paths.capacity)) * 0.1).cuda()
-    gtx, grx, gobj = mpt.grad(ds, cands, paths, g_len, g_pts)
+    if not with_pts:
+        g_pts.zero_()
+    gtx, grx, gobj = mpt.grad(ds, cands, paths, g_len, g_pts if with_pts else None)
     torch.cuda.synchronize()
     table = oracle.enumerate_sequences(sc, 2, spec)
     cand = paths.cand[:n].cpu().numpy()
