@@ -251,9 +251,12 @@ struct GradView {
 // lanes of a warp agree), and each order gets registers of its own.  The
 // loop bounds are uniform over the block so that whole warps reach the
 // aggregated atomics together.
-template <int N>
-__global__ void __launch_bounds__(GRAD_BLOCK, (N <= 2 ? 3 : 1)) k_grad(DevScene sc, DevEnds ep, GradView gv,
-                                                                       double* g_tx, double* g_rx, double* g_obj) {
+// PTS: point weights given (the normal-matrix solve; few registers spare)
+// or not (explicit gradient only: a short kernel at full occupancy).
+template <int N, bool PTS>
+__global__ void __launch_bounds__(GRAD_BLOCK, (PTS ? (N <= 2 ? 3 : 1) : 4)) k_grad(DevScene sc, DevEnds ep,
+                                                                                  GradView gv, double* g_tx,
+                                                                                  double* g_rx, double* g_obj) {
   int64_t n = *gv.count;
   if (n > gv.pcap) n = gv.pcap;
   for (int64_t i0 = (int64_t)blockIdx.x * GRAD_BLOCK; i0 < n; i0 += (int64_t)gridDim.x * GRAD_BLOCK) {
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(GRAD_BLOCK, (N <= 2 ? 3 : 1)) k_grad(DevScene 
           for (int j = 0; j < 2 * N; ++j) Tc[j] = gv.pT[(int64_t)j * gv.pcap + i];
           double gX[3 * N];
           const double* gxp = nullptr;
-          if (gv.g_pts) {
+          if (PTS && gv.g_pts) {
 #pragma unroll
             for (int j = 0; j < 3 * N; ++j) gX[j] = gv.g_pts[(int64_t)j * gv.pcap + i];
             gxp = gX;
@@ -308,14 +311,19 @@ int launch_grad(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
   // the orders are independent (their sums meet only in atomics): order 2
   // on the caller's stream, orders 1, 3, 4 on the context's auxiliary streams
   MPT_CUDA_TRY(fork_streams(ctx, st));
-  k_grad<2><<<(unsigned)blocks, GRAD_BLOCK, 0, st>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
-  MPT_LAUNCH_CHECK();
-  k_grad<1><<<(unsigned)blocks, GRAD_BLOCK, 0, ctx->aux[0]>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
-  MPT_LAUNCH_CHECK();
-  k_grad<3><<<(unsigned)blocks, GRAD_BLOCK, 0, ctx->aux[1]>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
-  MPT_LAUNCH_CHECK();
-  k_grad<4><<<(unsigned)blocks, GRAD_BLOCK, 0, ctx->aux[2]>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);
-  MPT_LAUNCH_CHECK();
+#define MPT_GRAD(N, S)                                                                           \
+  {                                                                                              \
+    if (g_pts)                                                                                   \
+      k_grad<N, true><<<(unsigned)blocks, GRAD_BLOCK, 0, (S)>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);  \
+    else                                                                                         \
+      k_grad<N, false><<<(unsigned)blocks, GRAD_BLOCK, 0, (S)>>>(scene->d, ep, gv, g_tx, g_rx, g_obj); \
+    MPT_LAUNCH_CHECK();                                                                          \
+  }
+  MPT_GRAD(2, st)
+  MPT_GRAD(1, ctx->aux[0])
+  MPT_GRAD(3, ctx->aux[1])
+  MPT_GRAD(4, ctx->aux[2])
+#undef MPT_GRAD
   MPT_CUDA_TRY(join_streams(ctx, st));
   return MPT_OK;
 }
