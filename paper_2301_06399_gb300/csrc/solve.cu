@@ -553,9 +553,26 @@ __device__ __forceinline__ bool clearly_crosses(const float4* sm, int n_occ, int
   return uu > CLEAR_M && uu < f0.w - CLEAR_M && vv > CLEAR_M && vv < f1.w - CLEAR_M;
 }
 
+// Does the segment A + t d, t in [0, 1], meet the box [lo, hi]?  Slab test
+// with inv = 1/d per axis (infinite for an axis the segment does not move
+// along).  A NaN (an end exactly on a face plane of an axis it does not move
+// along) counts as a miss; the boxes are grown by 1 cm around their
+// occluders, so such a segment cannot cross one.
+__device__ __forceinline__ bool seg_box(const v3<float>& A, const v3<float>& inv, const float4& lo,
+                                        const float4& hi) {
+  const float x1 = (lo.x - A.x) * inv.x, x2 = (hi.x - A.x) * inv.x;
+  const float y1 = (lo.y - A.y) * inv.y, y2 = (hi.y - A.y) * inv.y;
+  const float z1 = (lo.z - A.z) * inv.z, z2 = (hi.z - A.z) * inv.z;
+  const float t0 = fmaxf(fmaxf(fminf(x1, x2), fminf(y1, y2)), fmaxf(fminf(z1, z2), 0.f));
+  const float t1 = fminf(fminf(fmaxf(x1, x2), fmaxf(y1, y2)), fminf(fmaxf(z1, z2), 1.f));
+  return t0 <= t1;
+}
+
 // Persistent grid over the first list; the occluders (records and boxes) are
-// staged in shared memory once per block.  Each occluder's box is loaded
-// once per candidate and tested against the boxes of all N + 1 segments.
+// staged in shared memory once per block.  For up to 32 groups at a time,
+// every lane first finds the groups whose boxes its segments meet (a
+// warp-uniform pass), then visits only those, so lanes with different
+// segments do not wait on each other's groups.
 template <int N>
 __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevEnds ep, const float4* ends32,
                                                                CandView cv, SolView out, RefineList rl1,
@@ -577,17 +594,18 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
     const int64_t i = i0 + threadIdx.x;
-    bool keep = false;
+    bool keep = false, test = false;
     int64_t c = 0;
+    v3<float> P[N + 2];
     if (i < n) {
       c = begin + rl1.idx[begin + i];
       if (c >= begin && c < end) {
         keep = true;
         if (out.cost[c] < (double)PRESCREEN_VIS_COST) {
+          test = true;
           const Cand cd = decode(__ldg(cv.rec + c));
           int it_, ir_;
           pair_ends(ep, cd.pair, it_, ir_);
-          v3<float> P[N + 2];
           P[0] = load_end<float>(ep.tx, ends32, it_);
           P[N + 1] = load_end<float>(ep.rx, ends32 + ep.n_tx, ir_);
 #pragma unroll
@@ -597,38 +615,53 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
             P[k + 1] = point_at<float, false>(kind, r, d2f_bits(out.T[(int64_t)(2 * k) * out.cap + c]),
                                               d2f_bits(out.T[(int64_t)(2 * k + 1) * out.cap + c])).X;
           }
-          v3<float> lo[N + 1], hi[N + 1];
+        }
+      }
+    }
+    bool blocked = false;
+    if (__ballot_sync(FULL, test)) {
+      v3<float> inv[N + 1], lo[N + 1], hi[N + 1];
 #pragma unroll
-          for (int j = 0; j <= N; ++j) {
-            lo[j] = mk(fminf(P[j].x, P[j + 1].x), fminf(P[j].y, P[j + 1].y), fminf(P[j].z, P[j + 1].z));
-            hi[j] = mk(fmaxf(P[j].x, P[j + 1].x), fmaxf(P[j].y, P[j + 1].y), fmaxf(P[j].z, P[j + 1].z));
-          }
-          bool blocked = false;
-          for (int gi = 0; gi < ng && !blocked; ++gi) {
-            const float4 gl = grp_sm[gi], gh = grp_sm[ng + gi];
-            bool any = false;
+      for (int j = 0; j <= N; ++j) {
+        if (test) {
+          inv[j] = mk(1.0f / (P[j + 1].x - P[j].x), 1.0f / (P[j + 1].y - P[j].y), 1.0f / (P[j + 1].z - P[j].z));
+          lo[j] = mk(fminf(P[j].x, P[j + 1].x), fminf(P[j].y, P[j + 1].y), fminf(P[j].z, P[j + 1].z));
+          hi[j] = mk(fmaxf(P[j].x, P[j + 1].x), fmaxf(P[j].y, P[j + 1].y), fmaxf(P[j].z, P[j + 1].z));
+        }
+      }
+      for (int g0 = 0; g0 < ng; g0 += 32) {
+        // groups g0 .. g0 + 31 that some segment of this lane meets
+        uint32_t gm = 0;
+        const int gn = ng - g0 < 32 ? ng - g0 : 32;
+        if (test && !blocked) {
+          for (int q = 0; q < gn; ++q) {
+            const float4 gl = grp_sm[g0 + q], gh = grp_sm[ng + g0 + q];
+            bool hit = false;
 #pragma unroll
-            for (int j = 0; j <= N; ++j)
-              any = any || (lo[j].x <= gh.x && hi[j].x >= gl.x && lo[j].y <= gh.y && hi[j].y >= gl.y &&
-                            lo[j].z <= gh.z && hi[j].z >= gl.z);
-            if (!any) continue;
-            const int o_end = (gi + 1) * OCC_GROUP < no ? (gi + 1) * OCC_GROUP : no;
-            for (int o = gi * OCC_GROUP; o < o_end && !blocked; ++o) {
-              const float4 bl = occ_sm[4 * no + o], bh = occ_sm[5 * no + o];
-              if (bl.w != 0.f) continue;  // rectangles only
-#pragma unroll
-              for (int j = 0; j <= N; ++j) {
-                if (lo[j].x <= bh.x && hi[j].x >= bl.x && lo[j].y <= bh.y && hi[j].y >= bl.y && lo[j].z <= bh.z &&
-                    hi[j].z >= bl.z)
-                  blocked = blocked || clearly_crosses(occ_sm, no, o, P[j], P[j + 1]);
-              }
-            }
-          }
-          if (blocked) {
-            out.status[c] = (uint8_t)(out.status[c] | MPT_PATH_PRESCREENED);
-            keep = false;
+            for (int j = 0; j <= N; ++j) hit = hit || seg_box(P[j], inv[j], gl, gh);
+            gm |= (uint32_t)hit << q;
           }
         }
+        while (gm != 0 && !blocked) {
+          const int gi = g0 + __ffs(gm) - 1;
+          gm &= gm - 1;
+          const int o_end = (gi + 1) * OCC_GROUP < no ? (gi + 1) * OCC_GROUP : no;
+          for (int o = gi * OCC_GROUP; o < o_end && !blocked; ++o) {
+            const float4 bl = occ_sm[4 * no + o], bh = occ_sm[5 * no + o];
+            if (bl.w != 0.f) continue;  // rectangles only
+#pragma unroll
+            for (int j = 0; j <= N; ++j) {
+              if (lo[j].x <= bh.x && hi[j].x >= bl.x && lo[j].y <= bh.y && hi[j].y >= bl.y && lo[j].z <= bh.z &&
+                  hi[j].z >= bl.z)
+                blocked = blocked || clearly_crosses(occ_sm, no, o, P[j], P[j + 1]);
+            }
+          }
+        }
+        if (__ballot_sync(FULL, test && !blocked) == 0) break;
+      }
+      if (blocked) {
+        out.status[c] = (uint8_t)(out.status[c] | MPT_PATH_PRESCREENED);
+        keep = false;
       }
     }
     const unsigned km = __ballot_sync(FULL, keep);
