@@ -42,6 +42,21 @@ __device__ __forceinline__ bool box_overlap(const float4& lo, const float4& hi, 
          fmaxf(A.y, B.y) >= lo.y && fminf(A.z, B.z) <= hi.z && fmaxf(A.z, B.z) >= lo.z;
 }
 
+// Does the segment A + t d, t in [0, 1], meet the box [lo, hi]?  Slab test
+// with inv = 1/d per axis (infinite for an axis the segment does not move
+// along).  A NaN (an end exactly on a face plane of an axis it does not move
+// along) counts as a miss; the boxes are grown by 1 cm around their
+// occluders, so such a segment cannot cross one.
+__device__ __forceinline__ bool seg_box(const v3<float>& A, const v3<float>& inv, const float4& lo,
+                                        const float4& hi) {
+  const float x1 = (lo.x - A.x) * inv.x, x2 = (hi.x - A.x) * inv.x;
+  const float y1 = (lo.y - A.y) * inv.y, y2 = (hi.y - A.y) * inv.y;
+  const float z1 = (lo.z - A.z) * inv.z, z2 = (hi.z - A.z) * inv.z;
+  const float t0 = fmaxf(fmaxf(fminf(x1, x2), fminf(y1, y2)), fmaxf(fminf(z1, z2), 0.f));
+  const float t1 = fminf(fminf(fmaxf(x1, x2), fmaxf(y1, y2)), fminf(fmaxf(z1, z2), 1.f));
+  return t0 <= t1;
+}
+
 struct DevEnds {
   const double* tx;
   const double* rx;

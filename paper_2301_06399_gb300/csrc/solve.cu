@@ -553,21 +553,6 @@ __device__ __forceinline__ bool clearly_crosses(const float4* sm, int n_occ, int
   return uu > CLEAR_M && uu < f0.w - CLEAR_M && vv > CLEAR_M && vv < f1.w - CLEAR_M;
 }
 
-// Does the segment A + t d, t in [0, 1], meet the box [lo, hi]?  Slab test
-// with inv = 1/d per axis (infinite for an axis the segment does not move
-// along).  A NaN (an end exactly on a face plane of an axis it does not move
-// along) counts as a miss; the boxes are grown by 1 cm around their
-// occluders, so such a segment cannot cross one.
-__device__ __forceinline__ bool seg_box(const v3<float>& A, const v3<float>& inv, const float4& lo,
-                                        const float4& hi) {
-  const float x1 = (lo.x - A.x) * inv.x, x2 = (hi.x - A.x) * inv.x;
-  const float y1 = (lo.y - A.y) * inv.y, y2 = (hi.y - A.y) * inv.y;
-  const float z1 = (lo.z - A.z) * inv.z, z2 = (hi.z - A.z) * inv.z;
-  const float t0 = fmaxf(fmaxf(fminf(x1, x2), fminf(y1, y2)), fmaxf(fminf(z1, z2), 0.f));
-  const float t1 = fminf(fminf(fmaxf(x1, x2), fmaxf(y1, y2)), fminf(fmaxf(z1, z2), 1.f));
-  return t0 <= t1;
-}
-
 // Persistent grid over the first list; the occluders (records and boxes) are
 // staged in shared memory once per block.  For up to 32 groups at a time,
 // every lane first finds the groups whose boxes its segments meet (a

@@ -222,30 +222,40 @@ __device__ bool accept_one(const DevScene& sc, const DevEnds& ep, const Cand& cd
     const v3<double> e = point64<N>(sc, ep, cd, Tc, it_, ir_, j + 1) - point64<N>(sc, ep, cd, Tc, it_, ir_, j);
     if (!(sqrt(dot(e, e)) >= lmin)) return false;
   }
-  // visibility of every segment against every occluder
+  // visibility of every segment against every occluder: for up to 32 groups
+  // at a time, the groups whose boxes the segment meets (a warp-uniform
+  // pass), then only their occluders
+  const float4* grp_sm = occ_sm + 6 * sc.n_occ;  // [2][n_grp]
+  const int ng = sc.n_grp;
 #pragma unroll
   for (int j = 0; j <= N; ++j) {
     const v3<float> Af = P[j], Bf = P[j + 1];
+    const v3<float> inv = mk(1.0f / (Bf.x - Af.x), 1.0f / (Bf.y - Af.y), 1.0f / (Bf.z - Af.z));
     // rectangles whose plane holds an end of this segment cannot be crossed
     // strictly (both ends must be more than EPS_VIS off the plane)
     const int4 none = make_int4(-1, -1, -1, -1);
     const int4 own0 = j >= 1 ? sc.obj_occ[cd.ids[j - 1]] : none;
     const int4 own1 = j < N ? sc.obj_occ[cd.ids[j]] : none;
-    const float4* grp_sm = occ_sm + 6 * sc.n_occ;  // [2][n_grp]
-    for (int gi = 0; gi < sc.n_grp; ++gi) {
-      if (!box_overlap(grp_sm[gi], grp_sm[sc.n_grp + gi], Af, Bf)) continue;
-      const int o_end = (gi + 1) * OCC_GROUP < sc.n_occ ? (gi + 1) * OCC_GROUP : sc.n_occ;
-      for (int o = gi * OCC_GROUP; o < o_end; ++o) {
-        if (!box_overlap(occ_sm[4 * sc.n_occ + o], occ_sm[5 * sc.n_occ + o], Af, Bf)) continue;
-        if (o == own0.x || o == own0.y || o == own0.z || o == own0.w || o == own1.x || o == own1.y ||
-            o == own1.z || o == own1.w)
-          continue;
-        int b = sc.occ_kind[o] == 0 ? rect32(occ_sm, sc.n_occ, o, Af, Bf) : -1;
-        if (b < 0)
-          b = blocks64(sc, o, point64<N>(sc, ep, cd, Tc, it_, ir_, j), point64<N>(sc, ep, cd, Tc, it_, ir_, j + 1))
-                  ? 1
-                  : 0;
-        if (b) return false;
+    for (int g0 = 0; g0 < ng; g0 += 32) {
+      uint32_t gm = 0;
+      const int gn = ng - g0 < 32 ? ng - g0 : 32;
+      for (int q = 0; q < gn; ++q) gm |= (uint32_t)seg_box(Af, inv, grp_sm[g0 + q], grp_sm[ng + g0 + q]) << q;
+      while (gm != 0) {
+        const int gi = g0 + __ffs(gm) - 1;
+        gm &= gm - 1;
+        const int o_end = (gi + 1) * OCC_GROUP < sc.n_occ ? (gi + 1) * OCC_GROUP : sc.n_occ;
+        for (int o = gi * OCC_GROUP; o < o_end; ++o) {
+          if (!box_overlap(occ_sm[4 * sc.n_occ + o], occ_sm[5 * sc.n_occ + o], Af, Bf)) continue;
+          if (o == own0.x || o == own0.y || o == own0.z || o == own0.w || o == own1.x || o == own1.y ||
+              o == own1.z || o == own1.w)
+            continue;
+          int b = sc.occ_kind[o] == 0 ? rect32(occ_sm, sc.n_occ, o, Af, Bf) : -1;
+          if (b < 0)
+            b = blocks64(sc, o, point64<N>(sc, ep, cd, Tc, it_, ir_, j), point64<N>(sc, ep, cd, Tc, it_, ir_, j + 1))
+                    ? 1
+                    : 0;
+          if (b) return false;
+        }
       }
     }
   }
@@ -259,7 +269,7 @@ constexpr int FLAG_PER_THREAD = GROUP / ACC_BLOCK;   // candidates per k_flag th
 constexpr uint32_t LIST_SKIP = 0xFFFFFFFFu;          // list entry of a group that did not fit
 
 struct ValScratch {
-  unsigned long long* list_n;  // [1] list entries claimed
+  unsigned long long* list_n;  // [2] list entries claimed; cursor of k_accept_list
   uint32_t* grp_count;         // [n_groups] valid paths per group
   uint32_t* words;             // [n_groups * GROUP_WORDS] one bit per valid candidate
   int64_t* grp_off;            // [n_groups] output position of the group's first path
@@ -422,21 +432,31 @@ __global__ void __launch_bounds__(ACC_BLOCK) k_flag(AccView av, double tau, ValS
   }
 }
 
-// Persistent grid over the list entries, one candidate per thread.
-__global__ void __launch_bounds__(ACC_BLOCK) k_accept_list(DevScene sc, DevEnds ep, AccView av, ValScratch vs,
-                                                           int* err_flag) {
+// Persistent grid over the list entries, one candidate per thread; warps
+// claim 32 entries at a time from a cursor (vs.list_n[1]), so that blocks
+// that meet cheap candidates take more of them.
+constexpr int LIST_BLOCK = 128;
+__global__ void __launch_bounds__(LIST_BLOCK, 3) k_accept_list(DevScene sc, DevEnds ep, AccView av, ValScratch vs,
+                                                            int* err_flag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   float4* occ_sm = reinterpret_cast<float4*>(smem_raw);
   unsigned long long n = *vs.list_n;
   if (n > (unsigned long long)vs.list_cap) n = (unsigned long long)vs.list_cap;
-  if ((unsigned long long)blockIdx.x * ACC_BLOCK >= n) return;  // the whole block
+  if (n == 0) return;  // the whole block
   if (!stage_occluders(sc, occ_sm, &bar, err_flag)) return;
-  for (unsigned long long i = (unsigned long long)blockIdx.x * ACC_BLOCK + threadIdx.x; i < n;
-       i += (unsigned long long)gridDim.x * ACC_BLOCK) {
-    const uint32_t c = vs.list[i];
-    if (c == LIST_SKIP || (int64_t)c >= av.cap) continue;
-    if (accept_candidate(sc, ep, av, c, occ_sm)) mark_valid(vs, c);
+  unsigned long long* cursor = vs.list_n + 1;
+  const unsigned lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(cursor, 32ull);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if (b >= n) break;
+    const unsigned long long i = b + lane;
+    if (i < n) {
+      const uint32_t c = vs.list[i];
+      if (c != LIST_SKIP && (int64_t)c < av.cap && accept_candidate(sc, ep, av, c, occ_sm)) mark_valid(vs, c);
+    }
   }
 }
 
@@ -595,13 +615,13 @@ static int run_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoint
     cudaFuncSetAttribute(k_accept_ovf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_accept_list, ACC_BLOCK, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_accept_list, LIST_BLOCK, smem);
   if (occ < 1) occ = 1;
   int64_t grid = (int64_t)ctx->sms * occ;
-  const int64_t need = (list_cap + ACC_BLOCK - 1) / ACC_BLOCK;
+  const int64_t need = (list_cap + LIST_BLOCK - 1) / LIST_BLOCK;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  k_accept_list<<<(unsigned)grid, ACC_BLOCK, smem, st>>>(scene->d, ep, av, vs, ctx->err_flag);
+  k_accept_list<<<(unsigned)grid, LIST_BLOCK, smem, st>>>(scene->d, ep, av, vs, ctx->err_flag);
   MPT_LAUNCH_CHECK();
   if (may_overflow) {
     k_accept_ovf<<<(unsigned)n_groups, ACC_BLOCK, smem, st>>>(scene->d, ep, av, tau, vs, ctx->err_flag);
