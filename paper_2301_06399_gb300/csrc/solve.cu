@@ -553,7 +553,7 @@ __device__ __forceinline__ bool clearly_crosses(const float4* sm, int n_occ, int
   return uu > CLEAR_M && uu < f0.w - CLEAR_M && vv > CLEAR_M && vv < f1.w - CLEAR_M;
 }
 
-// Persistent grid over the first list; the occluders (records and boxes) are
+// Warps claim the first list 32 entries at a time; the occluders (records and boxes) are
 // staged in shared memory once per block.  For up to 32 groups at a time,
 // every lane first finds the groups whose boxes its segments meet (a
 // warp-uniform pass), then visits only those, so lanes with different
@@ -561,7 +561,7 @@ __device__ __forceinline__ bool clearly_crosses(const float4* sm, int n_occ, int
 template <int N>
 __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevEnds ep, const float4* ends32,
                                                                CandView cv, SolView out, RefineList rl1,
-                                                               RefineList rl2) {
+                                                               RefineList rl2, unsigned long long* cursor) {
   extern __shared__ float4 occ_sm[];  // [6][n_occ] records and boxes, then [2][n_grp] group boxes
   int64_t end = cv.order_begin[N];
   if (end > cv.cap) end = cv.cap;
@@ -569,16 +569,20 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
   if (begin > end) begin = end;
   int64_t n = (int64_t)rl1.count[N - 1];
   if (n > end - begin) n = end - begin;
-  if ((int64_t)blockIdx.x * blockDim.x >= n) return;  // the whole block
+  if (n <= 0) return;  // the whole block
   const int no = sc.n_occ, ng = sc.n_grp;
   for (int q = threadIdx.x; q < 6 * no + 2 * ng; q += blockDim.x)
     occ_sm[q] = q < 4 * no ? __ldg(sc.c32 + q) : q < 6 * no ? __ldg(sc.cbox + (q - 4 * no)) : __ldg(sc.gbox + (q - 6 * no));
   __syncthreads();
   const float4* grp_sm = occ_sm + 6 * no;  // [2][ng]
   const unsigned lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
-    const int64_t i = i0 + threadIdx.x;
+  // warps claim 32 list entries at a time
+  for (;;) {
+    unsigned long long wb = 0;
+    if (lane == 0) wb = atomicAdd(cursor, 32ull);
+    wb = __shfl_sync(FULL, wb, 0);
+    if ((int64_t)wb >= n) break;
+    const int64_t i = (int64_t)wb + lane;
     bool keep = false, test = false;
     int64_t c = 0;
     v3<float> P[N + 2];
@@ -728,7 +732,7 @@ constexpr float REFINE_STOP = 1e-24f, REFINE_TARGET = 1e-22f;
 template <int N>
 __global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? 3 : 1)) k_refine(DevScene sc, DevEnds ep, CandView cv,
                                                                         SolView out, SolveCfg cfg, RefineList rl,
-                                                                        RefineList rl3) {
+                                                                        RefineList rl3, unsigned long long* cursor) {
   constexpr int Q = 2 * N;
   int64_t end = cv.order_begin[N];
   if (end > cv.cap) end = cv.cap;
@@ -738,8 +742,13 @@ __global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? 3 : 1)) k_refine(DevSce
   if (n > end - begin) n = end - begin;
   const ff stop(REFINE_STOP), target(REFINE_TARGET);
   const unsigned lane = threadIdx.x & 31;
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = i0 + threadIdx.x;
+  // warps claim 32 list entries at a time (refinement lengths vary)
+  for (;;) {
+    unsigned long long wb = 0;
+    if (lane == 0) wb = atomicAdd(cursor, 32ull);
+    wb = __shfl_sync(FULL, wb, 0);
+    if ((int64_t)wb >= n) break;
+    const int64_t i = (int64_t)wb + lane;
     bool fallback = false;
     int64_t c = 0;
     if (i < n) {
@@ -856,8 +865,9 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
                        RefineList rl2, bool curved, cudaStream_t st) {
   // counters[0..3]: per-order candidate cursors; [4]: mixed-order cursor;
   // [8..11]: refine list sizes; [12..15]: sizes after the visibility
-  // prescreen; [16..19]: fallback queue sizes
-  MPT_CUDA_TRY(cudaMemsetAsync(ctx->counters, 0, 20 * sizeof(unsigned long long), st));
+  // prescreen; [16..19]: fallback queue sizes; [20..23]: refinement
+  // cursors; [24..27]: prescreen cursors
+  MPT_CUDA_TRY(cudaMemsetAsync(ctx->counters, 0, 28 * sizeof(unsigned long long), st));
   const size_t vsmem = (size_t)sc.n_occ * 96 + (size_t)sc.n_grp * 32;
   // the fallback queue reuses the first list's storage (read by then)
   const RefineList rl3{ctx->counters + 16, rl.idx};
@@ -888,9 +898,10 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
       if (vsmem > 48 * 1024)                                                                                   \
         cudaFuncSetAttribute(k_vis_prescreen<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem);     \
       k_vis_prescreen<N><<<grid_for(ctx, k_vis_prescreen<N>, nullptr, vsmem), SOLVE_BLOCK, vsmem, s_>>>(       \
-          sc, ep, ends32, cv, sv, rl, rl2);                                                                    \
+          sc, ep, ends32, cv, sv, rl, rl2, ctx->counters + 24 + (N - 1));                                      \
       MPT_LAUNCH_CHECK();                                                                                      \
-      k_refine<N><<<grid_for(ctx, k_refine<N>, nullptr), SOLVE_BLOCK, 0, s_>>>(sc, ep, cv, sv, cfg, rl2, rl3); \
+      k_refine<N><<<grid_for(ctx, k_refine<N>, nullptr), SOLVE_BLOCK, 0, s_>>>(sc, ep, cv, sv, cfg, rl2, rl3,   \
+                                                                               ctx->counters + 20 + (N - 1));   \
       MPT_LAUNCH_CHECK();                                                                                      \
       k_refine_fb<N><<<ctx->sms * 4, 32, 0, s_>>>(sc, ep, cv, sv, cfg, rl3);                                   \
       MPT_LAUNCH_CHECK();                                                                                      \
