@@ -677,28 +677,45 @@ template <int N>
 __device__ ff gn_ff(const int (&kind)[N], const Rec<ff> (&rec)[N], ff (&prm)[2 * N], const v3<ff>& A,
                     const v3<ff>& B, int max_iters, float mu, float stop) {
   constexpr int Q = 2 * N, P = Q * (Q + 1) / 2;
-  ff jtj[P], g[Q], dlt[Q], trial[Q];
-  bool ok;
-  ff cost = eval_path<N, ff, ff, true>(kind, rec, prm, A, B, jtj, g, ok);
-  if (!ok) return ff((float)INFINITY);
+  ff jtj[P], g[Q], dlt[Q], trial[Q], jt2[P], g2[Q];
+  ff cost((float)INFINITY);
   float alpha = 1.0f;
   bool need_factor = true;
-  for (int it = 0; it < 2 * max_iters && cost.hi >= stop; ++it) {
-    if (need_factor) {
-      pin_unused<N, ff>(kind, jtj, g);
-      cholesky<Q, ff>(jtj, ff(mu));
-      chol_solve<Q, ff>(jtj, g, dlt);
-      float pred = 0.f;
+  // one evaluation site (it = -1 evaluates the start): a second inlined copy
+  // of the float-float evaluation costs more in instruction fetch than the
+  // extra copies below
+#pragma unroll 1
+  for (int it = -1; it < 2 * max_iters; ++it) {
+    if (it >= 0) {
+      if (!(cost.hi >= stop)) break;
+      if (need_factor) {
+        pin_unused<N, ff>(kind, jtj, g);
+        cholesky<Q, ff>(jtj, ff(mu));
+        chol_solve<Q, ff>(jtj, g, dlt);
+        float pred = 0.f;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) pred = fmaf(-g[i].hi, dlt[i].hi, pred);
-      if (pred < 1e-3f * cost.hi) break;
-      alpha = 1.0f;
-      need_factor = false;
+        for (int i = 0; i < Q; ++i) pred = fmaf(-g[i].hi, dlt[i].hi, pred);
+        if (pred < 1e-3f * cost.hi) break;
+        alpha = 1.0f;
+        need_factor = false;
+      }
+#pragma unroll
+      for (int i = 0; i < Q; ++i) trial[i] = fma_(ff(alpha), dlt[i], prm[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) trial[i] = prm[i];
     }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) trial[i] = fma_(ff(alpha), dlt[i], prm[i]);
-    ff jt2[P], g2[Q];
+    bool ok;
     const ff ct = eval_path<N, ff, ff, true>(kind, rec, trial, A, B, jt2, g2, ok);
+    if (it < 0) {
+      if (!ok) return ff((float)INFINITY);
+      cost = ct;
+#pragma unroll
+      for (int i = 0; i < P; ++i) jtj[i] = jt2[i];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) g[i] = g2[i];
+      continue;
+    }
     if (ok && ct < cost) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) prm[i] = trial[i];
@@ -770,21 +787,28 @@ __global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? 3 : 1)) k_refine(DevSce
 #pragma unroll
         for (int j = 0; j < Q; ++j) T[j] = T0[j] = ff_from_double(out.T[(int64_t)j * out.cap + c]);
         float jtj[Q * (Q + 1) / 2], g[Q], dlt[Q];
-        bool ok;
-        ff cst = eval_path<N, ff, float, true>(kind, rec, T, A, B, jtj, g, ok);
-        ff prev = cst;
-        for (int s = 0; ok && cst >= stop; ++s) {
-          // beyond refine_steps, up to 6 more mixed steps while the target is
-          // not met and each step still halves the cost (slow linear
-          // convergence of ill-conditioned paths under the FP32 Jacobian)
-          if (s >= cfg.refine_steps && (s >= cfg.refine_steps + 6 || cst < target || !(cst.hi < 0.5f * prev.hi)))
-            break;
-          prev = cst;
-          pin_unused<N, float>(kind, jtj, g);
-          cholesky<Q, float>(jtj, cfg.mu32);
-          chol_solve<Q, float>(jtj, g, dlt);
+        bool ok = true;
+        ff cst(0.f), prev(0.f);
+        // one evaluation site (s = -1 evaluates the start): the float-float
+        // evaluation is long, and a second inlined copy costs more in
+        // instruction fetch than the loop control saves
+#pragma unroll 1
+        for (int s = -1;; ++s) {
+          if (s >= 0) {
+            if (!ok || !(cst >= stop)) break;
+            // beyond refine_steps, up to 6 more mixed steps while the target
+            // is not met and each step still halves the cost (slow linear
+            // convergence of ill-conditioned paths under the FP32 Jacobian)
+            if (s >= cfg.refine_steps &&
+                (s >= cfg.refine_steps + 6 || cst < target || !(cst.hi < 0.5f * prev.hi)))
+              break;
+            prev = cst;
+            pin_unused<N, float>(kind, jtj, g);
+            cholesky<Q, float>(jtj, cfg.mu32);
+            chol_solve<Q, float>(jtj, g, dlt);
 #pragma unroll
-          for (int j = 0; j < Q; ++j) T[j] = T[j] + ff(dlt[j]);
+            for (int j = 0; j < Q; ++j) T[j] = T[j] + ff(dlt[j]);
+          }
           cst = eval_path<N, ff, float, true>(kind, rec, T, A, B, jtj, g, ok);
         }
         fallback = !ok || !(cst < target);
