@@ -61,10 +61,18 @@ struct SolView {
 
 // Per-order refine lists: positions (candidate - first candidate of the
 // order) stored in idx[first of the order ...], counts in count[order - 1].
+// The first list (queued by the solver) also carries, per entry, bit 31 of
+// idx = "FP32 cost below the visibility-prescreen threshold" and the FP32
+// parameters in prm[j * stride + entry], so that the prescreen reads neither
+// the cost nor the FP64 parameters back.
 struct RefineList {
   unsigned long long* count;  // [4]
   int32_t* idx;               // [cap]
+  float* prm;                 // [8][stride] or null
+  int64_t stride;
 };
+constexpr int32_t RL_VIS = (int32_t)0x80000000;  // idx flag: prescreen the visibility
+constexpr float PRESCREEN_VIS_COST = 1e-10f;
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int CHUNK = 256;  // candidates a warp claims at once (8 per lane)
@@ -310,7 +318,12 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
           base = __shfl_sync(FULL, base, leader);
           if (done_push) {
             const int64_t pos = (int64_t)base + __popc(pm & lt_mask);
-            rl.idx[order_base + pos] = (int32_t)(begin + done_c - order_base);
+            const int64_t at = order_base + pos;
+            rl.idx[at] = (int32_t)(begin + done_c - order_base) | (cost < R(PRESCREEN_VIS_COST) ? RL_VIS : 0);
+            if (rl.prm != nullptr) {
+#pragma unroll
+              for (int i = 0; i < Q; ++i) rl.prm[(int64_t)i * rl.stride + at] = (float)prm[i];
+            }
           }
         }
       }
@@ -536,7 +549,6 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_mixed(DevScene sc, DevEnds e
 // magnitude less), so they are rejected here; the others go to the second
 // list that k_refine processes.  Paraboloid occluders never reject here.
 constexpr float CLEAR_M = 0.25f;
-constexpr float PRESCREEN_VIS_COST = 1e-10f;
 
 // Occluder o (staged in shared memory: fields 0-3 of the FP32 records, then
 // the boxes lo (w = kind) and hi) crosses segment AB with a clearance of
@@ -587,10 +599,11 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
     int64_t c = 0;
     v3<float> P[N + 2];
     if (i < n) {
-      c = begin + rl1.idx[begin + i];
+      const int32_t e = rl1.idx[begin + i];
+      c = begin + (e & ~RL_VIS);
       if (c >= begin && c < end) {
         keep = true;
-        if (out.cost[c] < (double)PRESCREEN_VIS_COST) {
+        if (e & RL_VIS) {
           test = true;
           const Cand cd = decode(__ldg(cv.rec + c));
           int it_, ir_;
@@ -601,8 +614,8 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
           for (int k = 0; k < N; ++k) {
             const int kind = __ldg(sc.kind + cd.ids[k]);
             const Rec<float> r = load_obj32(sc, cd.ids[k]);
-            P[k + 1] = point_at<float, false>(kind, r, d2f_bits(out.T[(int64_t)(2 * k) * out.cap + c]),
-                                              d2f_bits(out.T[(int64_t)(2 * k + 1) * out.cap + c])).X;
+            P[k + 1] = point_at<float, false>(kind, r, rl1.prm[(int64_t)(2 * k) * rl1.stride + begin + i],
+                                              rl1.prm[(int64_t)(2 * k + 1) * rl1.stride + begin + i]).X;
           }
         }
       }
@@ -971,8 +984,9 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
   RefineList rl{ctx->counters + 8, nullptr};
   RefineList rl2{ctx->counters + 12, nullptr};
   if (precision == MPT_FP32_FP64REFINE) {
-    // two lists of one 4-byte position per candidate: queued, then kept
-    const size_t need = 2 * (size_t)cand->capacity * sizeof(int32_t) + 256;
+    // two lists of one 4-byte position per candidate (queued, then kept) and
+    // the queued entries' FP32 parameters
+    const size_t need = 2 * (size_t)cand->capacity * sizeof(int32_t) + 8 * (size_t)cand->capacity * sizeof(float) + 512;
     if (ctx->rscratch_bytes < need) {
       if (ctx->rscratch) MPT_CUDA_TRY(cudaFreeAsync(ctx->rscratch, st));
       ctx->rscratch = nullptr;
@@ -982,6 +996,9 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
     }
     rl.idx = reinterpret_cast<int32_t*>(ctx->rscratch);
     rl2.idx = rl.idx + cand->capacity;
+    const size_t prm_off = ((2 * (size_t)cand->capacity * sizeof(int32_t)) + 255) & ~size_t(255);
+    rl.prm = reinterpret_cast<float*>(static_cast<unsigned char*>(ctx->rscratch) + prm_off);
+    rl.stride = cand->capacity;
   }
   // FP32 copies of the endpoints for the FP32 iterations
   const int n_ends = ends->n_tx + ends->n_rx;
