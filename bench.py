@@ -43,6 +43,19 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 FP32_LANES_PER_SM = 128
 
 
+def max_over_ranks(x: float, dev=None) -> float:
+    """Max of a per-rank scalar over the process group: the whole job takes
+    as long as its slowest rank.  gloo reduces CPU tensors, NCCL device ones."""
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    d = torch.device("cpu") if dist.get_backend() == "gloo" or dev is None else dev
+    t = torch.tensor([float(x)], dtype=torch.float64, device=d)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -270,10 +283,7 @@ def run_ours(args):
         step_ms = [a.elapsed_time(b) for a, b in ev_step]
         solve_ms = [a.elapsed_time(b) for a, b in ev_solve]
         total_ms = float(sum(step_ms))
-        if ws > 1:
-            t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dev)
         ms_per_step = total_ms / args.steps
         value = n_cand * ws / (ms_per_step * 1e-3)
 
@@ -403,10 +413,7 @@ def run_ours(args):
             d2h_bytes = 8 + nv * (8 + 12 * 8 + 8) + out_gtx.numel() * 8
             ds_e.free()
         e2e_ms_step = float(np.median(e2e_ms))
-        if ws > 1:
-            t = torch.tensor([e2e_ms_step], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms_step = float(t.item())
+        e2e_ms_step = max_over_ranks(e2e_ms_step, dev)
 
     solve_avg_ms = float(np.mean(solve_ms))
     achieved = flops / (solve_avg_ms * 1e-3) / 1e12
@@ -523,7 +530,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "candidates_per_step": per_step * n_pairs,
-                   "note": "FP64 CPU oracle (Levenberg-Marquardt, dual-number Jacobians) on the host cores"},
+                   "note": "FP64 CPU oracle (Gauss-Newton with backtracking, dual-number Jacobians) on the host cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
