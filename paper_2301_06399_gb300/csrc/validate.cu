@@ -385,11 +385,24 @@ __global__ void __launch_bounds__(ACC_BLOCK) k_flag(AccView av, double tau, ValS
   if (count > av.cap) count = av.cap;
   const int64_t g = blockIdx.x;
   const int64_t c0 = g * GROUP;
+  // thread t owns candidates c0 + FLAG_PER_THREAD t + j: their status bytes
+  // come in one 8-byte load when the buffer allows it
+  static_assert(FLAG_PER_THREAD == 8, "one 8-byte status load per thread");
+  const int64_t ct = c0 + (int64_t)FLAG_PER_THREAD * threadIdx.x;
   uint32_t mask = 0;
+  if (ct + FLAG_PER_THREAD <= count && (reinterpret_cast<uintptr_t>(av.status) & 7u) == 0) {
+    const uint2 st = *reinterpret_cast<const uint2*>(av.status + ct);
 #pragma unroll
-  for (int j = 0; j < FLAG_PER_THREAD; ++j) {
-    const int64_t c = c0 + (int64_t)j * ACC_BLOCK + threadIdx.x;
-    if (c < count && wanted(av, c, tau)) mask |= 1u << j;
+    for (int j = 0; j < FLAG_PER_THREAD; ++j) {
+      const uint32_t b = ((j < 4 ? st.x : st.y) >> (8 * (j & 3))) & 0xFFu;
+      if ((b & MPT_PATH_REFINED) && av.cost[ct + j] < tau) mask |= 1u << j;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < FLAG_PER_THREAD; ++j) {
+      const int64_t c = ct + j;
+      if (c < count && wanted(av, c, tau)) mask |= 1u << j;
+    }
   }
   const uint32_t n = __popc(mask);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -425,7 +438,7 @@ __global__ void __launch_bounds__(ACC_BLOCK) k_flag(AccView av, double tau, ValS
 #pragma unroll
     for (int j = 0; j < FLAG_PER_THREAD; ++j) {
       if (!((mask >> j) & 1u)) continue;
-      if (s_fit) vs.list[pos] = (uint32_t)(c0 + (int64_t)j * ACC_BLOCK + threadIdx.x);
+      if (s_fit) vs.list[pos] = (uint32_t)(ct + j);
       else if (pos < (unsigned long long)vs.list_cap) vs.list[pos] = LIST_SKIP;
       ++pos;
     }
