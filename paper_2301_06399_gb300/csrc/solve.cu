@@ -62,13 +62,16 @@ struct SolView {
 // Per-order refine lists: positions (candidate - first candidate of the
 // order) stored in idx[first of the order ...], counts in count[order - 1].
 // The first list (queued by the solver) also carries, per entry, bit 31 of
-// idx = "FP32 cost below the visibility-prescreen threshold" and the FP32
-// parameters in prm[j * stride + entry], so that the prescreen reads neither
-// the cost nor the FP64 parameters back.
+// idx = "FP32 cost below the visibility-prescreen threshold", the FP32
+// parameters in prm[j * stride + entry] and the object ids and endpoint
+// indices in ends[entry] (ids01, ids23, TX index, RX index), so that the
+// prescreen reads neither the candidate record, the cost nor the FP64
+// parameters back.
 struct RefineList {
   unsigned long long* count;  // [4]
   int32_t* idx;               // [cap]
   float* prm;                 // [8][stride] or null
+  uint4* ends;                // [stride] or null
   int64_t stride;
 };
 constexpr int32_t RL_VIS = (int32_t)0x80000000;  // idx flag: prescreen the visibility
@@ -323,6 +326,7 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
             if (rl.prm != nullptr) {
 #pragma unroll
               for (int i = 0; i < Q; ++i) rl.prm[(int64_t)i * rl.stride + at] = (float)prm[i];
+              rl.ends[at] = make_uint4(ids01, ids23, (uint32_t)it_, (uint32_t)ir_);
             }
           }
         }
@@ -605,15 +609,14 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
         keep = true;
         if (e & RL_VIS) {
           test = true;
-          const Cand cd = decode(__ldg(cv.rec + c));
-          int it_, ir_;
-          pair_ends(ep, cd.pair, it_, ir_);
-          P[0] = load_end<float>(ep.tx, ends32, it_);
-          P[N + 1] = load_end<float>(ep.rx, ends32 + ep.n_tx, ir_);
+          const uint4 q = rl1.ends[begin + i];
+          P[0] = load_end<float>(ep.tx, ends32, (int)q.z);
+          P[N + 1] = load_end<float>(ep.rx, ends32 + ep.n_tx, (int)q.w);
 #pragma unroll
           for (int k = 0; k < N; ++k) {
-            const int kind = __ldg(sc.kind + cd.ids[k]);
-            const Rec<float> r = load_obj32(sc, cd.ids[k]);
+            const int id = (int)(((k < 2 ? q.x : q.y) >> (16 * (k & 1))) & 0xFFFFu);
+            const int kind = __ldg(sc.kind + id);
+            const Rec<float> r = load_obj32(sc, id);
             P[k + 1] = point_at<float, false>(kind, r, rl1.prm[(int64_t)(2 * k) * rl1.stride + begin + i],
                                               rl1.prm[(int64_t)(2 * k + 1) * rl1.stride + begin + i]).X;
           }
@@ -984,9 +987,10 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
   RefineList rl{ctx->counters + 8, nullptr};
   RefineList rl2{ctx->counters + 12, nullptr};
   if (precision == MPT_FP32_FP64REFINE) {
-    // two lists of one 4-byte position per candidate (queued, then kept) and
-    // the queued entries' FP32 parameters
-    const size_t need = 2 * (size_t)cand->capacity * sizeof(int32_t) + 8 * (size_t)cand->capacity * sizeof(float) + 512;
+    // two lists of one 4-byte position per candidate (queued, then kept),
+    // the queued entries' FP32 parameters and their ids and endpoints
+    const size_t need = 2 * (size_t)cand->capacity * sizeof(int32_t) + 8 * (size_t)cand->capacity * sizeof(float) +
+                        (size_t)cand->capacity * sizeof(uint4) + 1024;
     if (ctx->rscratch_bytes < need) {
       if (ctx->rscratch) MPT_CUDA_TRY(cudaFreeAsync(ctx->rscratch, st));
       ctx->rscratch = nullptr;
@@ -998,6 +1002,8 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
     rl2.idx = rl.idx + cand->capacity;
     const size_t prm_off = ((2 * (size_t)cand->capacity * sizeof(int32_t)) + 255) & ~size_t(255);
     rl.prm = reinterpret_cast<float*>(static_cast<unsigned char*>(ctx->rscratch) + prm_off);
+    const size_t ends_off = (prm_off + 8 * (size_t)cand->capacity * sizeof(float) + 255) & ~size_t(255);
+    rl.ends = reinterpret_cast<uint4*>(static_cast<unsigned char*>(ctx->rscratch) + ends_off);
     rl.stride = cand->capacity;
   }
   // FP32 copies of the endpoints for the FP32 iterations
