@@ -181,6 +181,50 @@ __global__ void __launch_bounds__(SEQ_THREADS) k_sequences(SeqParams sp, const i
   if (tid == 0) entry_begin[4] = s_base;
 }
 
+// Full enumeration without a mask or curved objects: every sequence is one
+// entry, so entry e of order n sits at off[n - 1] + its lexicographic rank
+// and the table is written in parallel (no scan).  32-bit unranking: the
+// table holds fewer than 2^24 entries.
+struct FullSeq {
+  int n_obj;
+  int64_t off[5];  // first entry of orders 1..4, then the total
+};
+__global__ void k_sequences_full(FullSeq fs, Entry* table, int64_t table_cap, int64_t* entry_begin) {
+  const int64_t total = fs.off[4] < table_cap ? fs.off[4] : table_cap;
+  const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g0 < 5) entry_begin[g0] = fs.off[g0];
+  for (int64_t g = g0; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+    int n = 1;
+    while (n < 4 && g >= fs.off[n]) ++n;
+    uint32_t r = (uint32_t)(g - fs.off[n - 1]);
+    int ids[4] = {-1, -1, -1, -1};
+    int srt[4];
+    int nu = 0;
+    for (int k = 0; k < n; ++k) {
+      uint32_t rest = 1;
+      for (int j = 0; j < n - 1 - k; ++j) rest *= (uint32_t)(fs.n_obj - 1 - k - j);
+      const uint32_t idx = r / rest;
+      r -= idx * rest;
+      // idx-th id not yet used, walking the used ids in increasing order
+      int o = (int)idx;
+      for (int i = 0; i < nu; ++i)
+        if (srt[i] <= o) ++o;
+      ids[k] = o;
+      int j = nu++;
+      while (j > 0 && srt[j - 1] > o) {
+        srt[j] = srt[j - 1];
+        --j;
+      }
+      srt[j] = o;
+    }
+    Entry en;
+    en.ids01 = (uint32_t)(ids[0] & 0xFFFF) | ((uint32_t)(ids[1] & 0xFFFF) << 16);
+    en.ids23 = (uint32_t)(ids[2] & 0xFFFF) | ((uint32_t)(ids[3] & 0xFFFF) << 16);
+    en.meta = (uint32_t)n;
+    table[g] = en;
+  }
+}
+
 __global__ void k_expand(const Entry* table, int64_t table_cap, const int64_t* entry_begin, int64_t n_pairs,
                          uint4* rec, int64_t cap, int64_t* count, int64_t* order_begin) {
   int64_t E = entry_begin[4];
@@ -260,7 +304,24 @@ int launch_enumerate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* 
   MPT_CUDA_TRY(cudaMallocAsync(&buf, bytes, st));
   int64_t* entry_begin = reinterpret_cast<int64_t*>(buf);
   Entry* table = reinterpret_cast<Entry*>(entry_begin + 8);
-  k_sequences<<<1, SEQ_THREADS, 0, st>>>(sp, scene->d.kind, adj, table, table_cap, entry_begin);
+  bool full = adj == nullptr;
+  for (int i = 0; i < sp.n_obj && full; ++i) full = scene->host_kind[i] != K_PARAB && scene->host_kind[i] != K_ARC;
+  for (int n = 1; n <= 4 && full; ++n)
+    full = (n <= sp.max_order && n <= sp.n_obj) ? sp.quota[n - 1] <= 0 : true;
+  if (full) {
+    FullSeq fs;
+    fs.n_obj = sp.n_obj;
+    fs.off[0] = 0;
+    for (int n = 1; n <= 4; ++n) {
+      const bool on = n <= sp.max_order && n <= sp.n_obj && sp.quota[n - 1] < 0;
+      fs.off[n] = fs.off[n - 1] + (on ? perm_count(sp.n_obj, n) : 0);
+    }
+    const int64_t blocks = (fs.off[4] + 255) / 256;
+    k_sequences_full<<<(unsigned)(blocks < 1 ? 1 : (blocks > 4096 ? 4096 : blocks)), 256, 0, st>>>(fs, table, table_cap,
+                                                                                                 entry_begin);
+  } else {
+    k_sequences<<<1, SEQ_THREADS, 0, st>>>(sp, scene->d.kind, adj, table, table_cap, entry_begin);
+  }
   MPT_LAUNCH_CHECK();
   bool over = false;
   if (adj != nullptr) {
