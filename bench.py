@@ -462,7 +462,7 @@ def run_ours(args):
         "wall_s_timed_region": t_wall,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sc, spec, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline_child(args.cpu_seconds, args.rx_side)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -493,6 +493,14 @@ def cpu_baseline(sc, spec, seconds: float) -> dict:
     return {"value": done / dt, "unit": UNIT, "cores": oracle.threads(0), "kind": "oracle",
             "sample": f"{used} random sequences x {n_pairs} RX = {done} candidates of the workload "
                       f"(solve + validate), {dt:.1f} s"}
+
+
+def cpu_baseline_child(seconds: float, rx_side: int) -> dict:
+    """cpu_baseline in a fresh process, so that the oracle's threads share the
+    host cores with nothing this process leaves running."""
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-only", "--cpu-seconds",
+                          str(seconds), "--rx-side", str(rx_side)], capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
 
 
 def run_reference(args):
@@ -547,7 +555,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-entries", type=int, default=64)
     ap.add_argument("--rx-side", type=int, default=32, help="RX grid side (32 = the benchmark workload)")
+    ap.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_baseline_only:
+        import oracle
+
+        oracle.build()
+        sc, spec = build_scene(0, args.rx_side)
+        print(json.dumps(cpu_baseline(sc, spec, args.cpu_seconds)), flush=True)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
