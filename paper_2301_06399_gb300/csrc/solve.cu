@@ -124,7 +124,7 @@ __device__ __forceinline__ float unit_draw(uint64_t seed, uint32_t pair, uint64_
 // Initial parameters (Algorithm 1, random_guess): start 0 projects TX (first
 // half of the sequence, 2k < n) or RX (second half) onto the object; starts
 // > 0 draw curved objects uniformly over their disc / angle range.
-template <class R>
+template <class R, bool CURVED = true>
 __device__ __forceinline__ void init_params(int kind, const Rec<R>& r, const v3<R>& Y, uint64_t seed,
                                             uint32_t pair, uint64_t packed, int start, int k, R& s, R& t) {
   t = R(0);
@@ -132,7 +132,8 @@ __device__ __forceinline__ void init_params(int kind, const Rec<R>& r, const v3<
     v3<R> w = Y - r.f3(0);
     s = dot(w, r.f3(4));
     t = dot(w, r.f3(8));
-  } else if (kind == K_LINE) {
+  } else if (!CURVED || kind == K_LINE) {
+    // (a solver built for planes and straight edges only sees these two)
     s = dot(Y - r.f3(0), r.f3(4));
   } else if (kind == K_PARAB) {
     if (start == 0) {
@@ -367,16 +368,17 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
             ids23 = rr.z;
             const v3<R> A = load_end<R>(ep.tx, ends32, it_);
             const v3<R> B = load_end<R>(ep.rx, ends32 + ep.n_tx, ir_);
-            const uint64_t packed = pack_ids(cd, N);
+            // the ids hash seeds the extra starts of curved objects only
+            const uint64_t packed = CURVED ? pack_ids(cd, N) : 0ull;
             kinds = 0;
             lm_ratio = R(cfg.localmin_ratio_planar);
 #pragma unroll
             for (int k = 0; k < N; ++k) {
               const int kd = __ldg(sc.kind + cd.ids[k]);
               kinds |= kd << (8 * k);
-              if (kd == K_PARAB || kd == K_ARC) lm_ratio = R(cfg.localmin_ratio);
-              init_params<R>(kd, load_obj<R>(sc, cd.ids[k]), (2 * k < N) ? A : B, cv.init_seed, cd.pair, packed,
-                             cd.start, k, trial[2 * k], trial[2 * k + 1]);
+              if (CURVED && (kd == K_PARAB || kd == K_ARC)) lm_ratio = R(cfg.localmin_ratio);
+              init_params<R, CURVED>(kd, load_obj<R>(sc, cd.ids[k]), (2 * k < N) ? A : B, cv.init_seed, cd.pair,
+                                     packed, cd.start, k, trial[2 * k], trial[2 * k + 1]);
             }
             fresh = true;
             iters = 0;
