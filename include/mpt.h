@@ -294,6 +294,13 @@ int mpt_validate_noalloc(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoin
  * MPT_ERR_TIMEOUT when a bounded device wait gave up since the last check. */
 int mpt_ctx_check(mpt_ctx* ctx, void* stream);
 
+/* Self-test of the failure path: enqueues on `stream` one thread that waits
+ * on a device flag nothing sets, with a bounded spin like the library's other
+ * device waits (under a second here), gives up, raises the context's error
+ * flag and returns.  The next mpt_ctx_check reports MPT_ERR_TIMEOUT and the
+ * context stays usable.  Returns MPT_OK once enqueued. */
+int mpt_ctx_selftest_wait(mpt_ctx* ctx, void* stream);
+
 /* ----------------------------------------------------------------- grad */
 
 /* Adjoint of converged paths (implicit-function theorem on rho(T, theta) = 0

@@ -166,6 +166,33 @@ int mpt_ctx_check(mpt_ctx* ctx, void* stream) {
   return flag == 0 ? MPT_OK : flag;
 }
 
+namespace mpt {
+// Waits on *flag (which nothing sets) for at most SELFTEST_SPINS polls
+// 128 ns apart, then raises the error flag: the library's bounded-wait
+// failure path, end to end.
+constexpr unsigned SELFTEST_SPINS = 1u << 21;
+__global__ void k_wait_selftest(const volatile int* flag, int* err_flag) {
+  unsigned spins = 0;
+  while (*flag == 0) {
+    if (++spins > SELFTEST_SPINS) {
+      atomicExch(err_flag, MPT_ERR_TIMEOUT);
+      return;
+    }
+    __nanosleep(128);
+  }
+}
+}  // namespace mpt
+
+int mpt_ctx_selftest_wait(mpt_ctx* ctx, void* stream) {
+  if (!ctx) return MPT_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // the last counter word is zeroed at context creation and never written
+  const int* flag = reinterpret_cast<const int*>(ctx->counters + 63);
+  mpt::k_wait_selftest<<<1, 1, 0, st>>>(flag, ctx->err_flag);
+  MPT_LAUNCH_CHECK();
+  return MPT_OK;
+}
+
 int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) {
   if (!ctx || !desc || !out) return MPT_ERR_ARG;
   *out = nullptr;

@@ -66,7 +66,8 @@ _lock = threading.Lock()
 # Every symbol include/mpt.h declares.
 SYMBOLS = ["mpt_ctx_create", "mpt_ctx_destroy", "mpt_ctx_sm_count", "mpt_ctx_check", "mpt_scene_upload",
            "mpt_scene_free", "mpt_enumerate", "mpt_candidate_count", "mpt_solve", "mpt_validate", "mpt_grad",
-           "mpt_status_string", "mpt_flop_model", "mpt_validate_noalloc", "mpt_visibility", "mpt_field"]
+           "mpt_status_string", "mpt_flop_model", "mpt_validate_noalloc", "mpt_visibility", "mpt_field",
+           "mpt_ctx_selftest_wait"]
 
 
 def library_path() -> str:
@@ -86,6 +87,7 @@ def lib():
             L.mpt_ctx_destroy.argtypes = [P]
             L.mpt_ctx_sm_count.argtypes = [P]
             L.mpt_ctx_check.argtypes = [P, P]
+            L.mpt_ctx_selftest_wait.argtypes = [P, P]
             L.mpt_scene_upload.argtypes = [P, C.POINTER(SceneDesc), C.POINTER(P)]
             L.mpt_scene_free.argtypes = [P]
             L.mpt_enumerate.argtypes = [P, P, C.POINTER(Endpoints), C.c_int, P, C.POINTER(Sampling),
@@ -153,6 +155,10 @@ class Context:
 
     def check(self, stream=None) -> int:
         return int(lib().mpt_ctx_check(self.h, _stream(stream)))
+
+    def selftest_wait(self, stream=None) -> int:
+        """Enqueue the bounded-wait self-test (mpt_ctx_selftest_wait)."""
+        return int(lib().mpt_ctx_selftest_wait(self.h, _stream(stream)))
 
     def close(self):
         if self.h:

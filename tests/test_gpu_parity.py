@@ -584,3 +584,21 @@ def test_received_field_matches_oracle(mpt, ctx):
     mag = oracle.path_field(sc, table, sol, ver, 0.0 + 1e-300, 1.0, abs(refl), abs(diff))  # sum of |contributions|
     assert np.all(np.abs(got - want) <= 2 * k * 3e-6 * np.abs(mag) + 1e-15)
     assert np.abs(want).max() > 0
+
+
+# ------------------------------------------------------- failure path ---
+def test_bounded_wait_reports_timeout_and_the_context_stays_usable(mpt, ctx):
+    """A device wait that gives up (a flag nothing sets, bounded spin) raises
+    the context's error flag; mpt_ctx_check reports MPT_ERR_TIMEOUT once and
+    clears it, and the context keeps working."""
+    assert ctx.check() == mpt.MPT_OK
+    assert ctx.selftest_wait() == mpt.MPT_OK
+    torch.cuda.synchronize()
+    assert ctx.check() == mpt.MPT_ERR_TIMEOUT
+    assert ctx.check() == mpt.MPT_OK
+    sc = S.street_canyon()
+    spec = S.CONFIG_SPECS["street_canyon"]
+    _, cands, _, paths = gpu_trace(mpt, ctx, sc, 2, spec)
+    table = oracle.enumerate_sequences(sc, 2, spec)
+    n_valid, _, _ = compare_entries(sc, table, paths, range(len(table)), sc.n_pairs)
+    assert n_valid == paths.n() > 0
