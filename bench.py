@@ -434,7 +434,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD if args.rx_side == 32 else f"{WORKLOAD} (rx grid {args.rx_side}x{args.rx_side})",
                    "candidates_per_gpu": n_cand, "max_order": 2,
-                   "precision": "fp32 iterations + fp64 refinement of prescreened candidates",
+                   "precision": "fp32 iterations; float-float refinement of prescreened candidates (fp64 results); fp64 acceptance decisions near the margins",
                    "step": "enumerate + solve + validate/compact + adjoint",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write), outside the step events",
                    "parallelism": f"weak: one process per GPU, {ws} GPU(s)"},
