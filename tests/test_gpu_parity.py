@@ -179,6 +179,26 @@ def test_street_canyon_ragged_pairs(mpt, ctx):
     compare_entries(sc, table, paths, range(len(table)), sc.n_pairs)
 
 
+def test_validation_with_unaligned_status_buffer(mpt, ctx):
+    """Caller buffers need no alignment: the same solutions validated with
+    their status bytes at an odd address (the acceptance's flag pass then
+    reads them one byte at a time) give the same valid paths."""
+    sc = S.urban_block(4)
+    spec = S.CONFIG_SPECS["urban_block"]
+    ds, cands, sols, paths = gpu_trace(mpt, ctx, sc, 2, spec)
+    n = paths.n()
+    raw = torch.zeros(sols.capacity + 8, dtype=torch.uint8, device="cuda")
+    odd = raw[3:3 + sols.capacity]
+    odd.copy_(sols.status)
+    shifted = mpt.Solutions(sols.T, sols.cost, odd, sols.iters, sols.evals, sols.T32, sols.capacity)
+    assert shifted.status.data_ptr() % 8 == 3
+    p2 = mpt.validate(ds, cands, shifted, capacity=cands.capacity)
+    torch.cuda.synchronize()
+    assert p2.n() == n > 0
+    assert torch.equal(p2.cand[:n], paths.cand[:n])
+    assert torch.equal(p2.X[:, :n], paths.X[:, :n])
+
+
 # ------------------------------------------------------------- urban block --
 def test_urban_block_small_all_candidates(mpt, ctx):
     sc = S.urban_block(4)
