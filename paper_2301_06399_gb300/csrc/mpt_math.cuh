@@ -102,15 +102,17 @@ MPT_HD float d2f_bits(double x) {
 // produced by the solver's magnitudes) become +-0.
 MPT_HD double f2d_bits(float f) {
 #if defined(__CUDA_ARCH__)
+  // 32-bit halves: the low word is the mantissa's last 3 bits shifted up;
+  // the high word is sign | exponent and mantissa shifted down by 3 with the
+  // exponent rebiased (127 -> 1023: + 896 << 20), or all-ones for Inf/NaN.
   const uint32_t u = __float_as_uint(f);
-  const uint64_t s = (uint64_t)(u >> 31) << 63;
-  const uint32_t e = (u >> 23) & 0xFFu;
-  const uint64_t m = (uint64_t)(u & 0x7FFFFFu) << 29;
-  uint64_t d;
-  if (e == 0) d = s;
-  else if (e == 0xFFu) d = s | (0x7FFull << 52) | m;
-  else d = s | ((uint64_t)(e + 896u) << 52) | m;
-  return __longlong_as_double((long long)d);
+  const uint32_t a = u & 0x7FFFFFFFu;
+  const uint32_t sign = u & 0x80000000u;
+  uint32_t hi = (a >> 3) + 0x38000000u;
+  if (a >= 0x7F800000u) hi = (a >> 3) | 0x7FF00000u;  // Inf, NaN
+  if (a < 0x00800000u) hi = 0u;                        // zero, subnormal -> 0
+  const uint32_t lo = a < 0x00800000u ? 0u : u << 29;
+  return __hiloint2double((int)(hi | sign), (int)lo);
 #else
   return (double)f;
 #endif
