@@ -498,9 +498,13 @@ def cpu_baseline(sc, spec, seconds: float) -> dict:
 def cpu_baseline_child(seconds: float, rx_side: int) -> dict:
     """cpu_baseline in a fresh process, so that the oracle's threads share the
     host cores with nothing this process leaves running."""
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-only", "--cpu-seconds",
-                          str(seconds), "--rx-side", str(rx_side)], capture_output=True, text=True, check=True)
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    try:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-only", "--cpu-seconds",
+                              str(seconds), "--rx-side", str(rx_side)], capture_output=True, text=True, check=True,
+                             timeout=600)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as exc:  # reported in the line, never replaced by a number
+        return {"error": f"{type(exc).__name__}: {exc}"[:300], "kind": "oracle"}
 
 
 def run_reference(args):
