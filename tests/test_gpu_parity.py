@@ -225,6 +225,52 @@ def test_urban_block_full_size_sampled(mpt, ctx):
           f" total valid {paths.n()}")
 
 
+def test_urban_block_full_size_adjoint(mpt, ctx):
+    """The adjoint in the benchmark's launch configuration (length weights,
+    157,792 paths): the accumulated dL/dTX, dL/dRX and plane-offset sums equal
+    the explicit gradient written out in numpy from the returned FP64 points
+    (-u_0 per path for TX, u_n for its RX, <u_m - u_m+1, n> for a reflection
+    on plane m), a property that holds at any size."""
+    sc = S.urban_block(32)
+    spec = S.CONFIG_SPECS["urban_block"]
+    ds, cands, sols, paths = gpu_trace(mpt, ctx, sc, 2, spec, path_cap=1 << 20)
+    n = paths.n()
+    g_len = torch.ones(paths.capacity, dtype=torch.float64, device="cuda")
+    gtx, grx, gobj = mpt.grad(ds, cands, paths, g_len)
+    torch.cuda.synchronize()
+    table = oracle.enumerate_sequences(sc, 2, spec)
+    cand = paths.cand[:n].cpu().numpy()
+    X = paths.X[:, :n].cpu().numpy().T
+    ent, pair = np.divmod(cand, sc.n_pairs)
+    order = table.order[ent]
+    A = np.repeat(sc.tx[:1], n, 0)
+    B = sc.rx[pair]
+    def unit(v):
+        with np.errstate(invalid="ignore", divide="ignore"):  # order-1 rows of u2 are unused
+            return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+    P1 = X[:, 0:3]
+    P2 = np.where((order == 2)[:, None], X[:, 3:6], B)
+    u0, u1 = unit(P1 - A), unit(P2 - P1)
+    u2 = unit(B - P2)
+    want_tx = -u0.sum(0)
+    last = np.where((order == 2)[:, None], u2, u1)
+    want_rx = np.zeros_like(sc.rx)
+    np.add.at(want_rx, pair, last)
+    want_obj = np.zeros(sc.n_obj)
+    planes = sc.obj_kind == 0
+    for k, (ui, uo) in enumerate(((u0, u1), (u1, u2))):
+        has = order > k
+        ids = table.ids[ent[has], k]
+        keep = planes[ids]
+        nrm = sc.obj_param[ids[keep], 0:3]
+        np.add.at(want_obj, ids[keep], ((ui[has][keep] - uo[has][keep]) * nrm).sum(1))
+    assert n == 157792
+    assert np.abs(gtx.cpu().numpy()[0] - want_tx).max() < 1e-9 * max(1.0, np.abs(want_tx).max())
+    assert np.abs(grx.cpu().numpy() - want_rx).max() < 1e-9 * max(1.0, np.abs(want_rx).max())
+    assert np.abs(gobj.cpu().numpy() - want_obj).max() < 1e-9 * max(1.0, np.abs(want_obj).max())
+
+
 # ------------------------------------------------------------ mixed orders --
 def test_mixed_orders_sampled(mpt, ctx):
     """Orders 1-4 (2,097,152 candidates incl. consecutive edge diffractions);
