@@ -63,6 +63,8 @@ def lib():
             L.oracle_validate.argtypes = [P, I64, P, P, I64, I64, I64, P, P, P, D, P, P, P, C.c_int]
             L.oracle_path_grad.restype = C.c_int
             L.oracle_path_grad.argtypes = [P, I32, P, P, P, P, P, P]
+            L.oracle_path_grad_many.restype = C.c_int
+            L.oracle_path_grad_many.argtypes = [P, I64, P, P, I64, P, P, P, P, P, C.c_int]
             L.oracle_residual.restype = C.c_int
             L.oracle_residual.argtypes = [P, I32, P, P, P, P, P, P]
             L.oracle_segment_blocked.restype = C.c_int
@@ -72,6 +74,8 @@ def lib():
             L.oracle_abi_version.restype = C.c_int
             L.oracle_splitmix64.restype = U64
             L.oracle_splitmix64.argtypes = [U64]
+            L.oracle_set_rules.restype = None
+            L.oracle_set_rules.argtypes = [I32, I32, D, I32]
             L.oracle_threads.restype = C.c_int
             L.oracle_threads.argtypes = [C.c_int]
             _lib = L
@@ -211,6 +215,63 @@ def path_grad(scene, ids, a, b, T):
     return dL, dX
 
 
+def pack_params(scene, table: SequenceTable, cand: np.ndarray, T_slots: np.ndarray) -> np.ndarray:
+    """Parameters given in two slots per interaction (slot 2k, 2k + 1; an
+    edge uses slot 2k only) packed in the oracle's order (an edge takes one
+    parameter, a surface two).  T_slots: float64 [n, 8]; returns [n, 8]."""
+    n = len(cand)
+    ent = np.asarray(cand, np.int64) // scene.n_pairs
+    ids = table.ids[ent]
+    order = table.order[ent]
+    kinds = np.asarray(scene.obj_kind)
+    out = np.zeros((n, 8), np.float64)
+    pos = np.zeros(n, np.int64)
+    rows = np.arange(n)
+    for k in range(4):
+        has = order > k
+        edge = np.zeros(n, bool)
+        edge[has] = np.isin(kinds[ids[has, k]], (2, 3))
+        r = rows[has]
+        out[r, pos[has]] = T_slots[r, 2 * k]
+        two = has & ~edge
+        out[rows[two], pos[two] + 1] = T_slots[rows[two], 2 * k + 1]
+        pos = pos + np.where(has, np.where(edge, 1, 2), 0)
+    return out
+
+
+def grad_sums(scene, table: SequenceTable, cand: np.ndarray, T_packed: np.ndarray, g_len: np.ndarray,
+              g_pts: np.ndarray | None = None, threads: int = 0):
+    """Sums over paths of the upstream-weighted implicit-function-theorem
+    gradient (oracle_path_grad per path): d/dTX [n_tx, 3], d/dRX [n_rx, 3]
+    and d/d(plane offset) [n_obj] (non-planar interactions add 0)."""
+    L = lib()
+    ref = SceneRef(scene)
+    cand = np.ascontiguousarray(cand, np.int64)
+    n = len(cand)
+    T = np.ascontiguousarray(T_packed, np.float64)
+    gl = np.ascontiguousarray(g_len, np.float64)
+    gp = None if g_pts is None else np.ascontiguousarray(g_pts, np.float64)
+    w = np.zeros((n, 10), np.float64)
+    bad = L.oracle_path_grad_many(ref.ptr, n, _p(table.order), _p(table.ids), scene.n_pairs, _p(cand), _p(T),
+                                  _p(gl), None if gp is None else _p(gp), _p(w), threads)
+    if bad:
+        raise RuntimeError(f"oracle_path_grad_many: {bad} singular normal matrices")
+    ent, pair = np.divmod(cand, scene.n_pairs)
+    n_rx = scene.rx.shape[0]
+    it, ir = (pair // n_rx, pair % n_rx) if scene.pair_mode == 0 else (pair, pair)
+    gtx = np.zeros_like(scene.tx)
+    grx = np.zeros_like(scene.rx)
+    gobj = np.zeros(scene.n_obj)
+    np.add.at(gtx, it, w[:, 0:3])
+    np.add.at(grx, ir, w[:, 3:6])
+    order = table.order[ent]
+    ids = table.ids[ent]
+    for k in range(4):
+        has = order > k
+        np.add.at(gobj, ids[has, k], w[has, 6 + k])
+    return gtx, grx, gobj
+
+
 def residual(scene, ids, a, b, T):
     """Stacked law residual (Eq. 10) and the points X(T)."""
     L = lib()
@@ -245,6 +306,16 @@ def params_in_bounds(scene, obj, u) -> tuple[bool, bool]:
     u = np.ascontiguousarray(np.asarray(u, np.float64).reshape(-1))
     r = L.oracle_params_in_bounds(ref.ptr, int(obj), _p(u), _p(amb))
     return bool(r), bool(amb[0])
+
+
+DEFAULT_RULES = dict(max_iters=24, max_evals=40, min_alpha=1.0 / 16.0, localmin_exit=True)
+
+
+def set_rules(max_iters: int = 24, max_evals: int = 40, min_alpha: float = 1.0 / 16.0,
+              localmin_exit: bool = True) -> None:
+    """Stopping rules of the oracle's minimiser (reading R15's values by
+    default).  A test hook: the rules apply to every later solve."""
+    lib().oracle_set_rules(int(max_iters), int(max_evals), float(min_alpha), int(bool(localmin_exit)))
 
 
 def splitmix64(x: int) -> int:

@@ -413,8 +413,20 @@ bool gn_step(int q, int m, const double* J, const double* rho, double* dx, doubl
 //     sequence is a plane or a straight edge and r = 1e-4 when a paraboloid
 //     or an arc edge is among them (curved objects bend the cost away from
 //     its linear model, and true paths can pass through such states).
+// The stopping rules above, held in one place so that a test can run the
+// oracle without its early exits (oracle_set_rules) and compare the valid
+// sets: the defaults are the rules the reading fixes.
+struct Rules {
+  int max_iters = 24;
+  int max_evals = 40;
+  double min_alpha = 1.0 / 16.0;
+  bool localmin_exit = true;
+};
+Rules g_rules;
+
 SolveOut gn_solve(const OracleScene& s, int n, const int32_t* ids, const double* a, const double* b,
                   const double* T0) {
+  const Rules rules = g_rules;
   SolveOut o;
   const int q = n_params(s, n, ids);
   bool curved = false;
@@ -455,16 +467,16 @@ SolveOut gn_solve(const OracleScene& s, int n, const int32_t* ids, const double*
         for (int i = 0; i < q; ++i) pmax = std::max(pmax, std::fabs(x[i]));
         if (!(pmax <= 1e3 * s.scale)) { o.status = ST_DIVERGED; break; }
         if (C < 1e-30 || smax < 1e-14 * s.scale) { o.status = ST_CONVERGED; break; }
-        if (o.iters >= 24) { o.status = ST_MAXITER; break; }
-        if (evals >= 40) { o.status = ST_MAXITER; break; }
+        if (o.iters >= rules.max_iters) { o.status = ST_MAXITER; break; }
+        if (evals >= rules.max_evals) { o.status = ST_MAXITER; break; }
         m = residual_jacobian(s, n, ids, a, b, x, rho, J);
         if (!gn_step(q, m, J, rho, dx, &pred)) { o.status = ST_STALLED; break; }
         alpha = 1.0;
-        if (o.iters >= 2 && C > 1e-3 && pred < lm_ratio * C) { o.status = ST_STALLED; break; }
+        if (rules.localmin_exit && o.iters >= 2 && C > 1e-3 && pred < lm_ratio * C) { o.status = ST_STALLED; break; }
       } else {
         alpha *= 0.5;
-        if (alpha < 1.0 / 16.0) { o.status = ST_STALLED; break; }
-        if (evals >= 40) { o.status = ST_MAXITER; break; }
+        if (alpha < rules.min_alpha) { o.status = ST_STALLED; break; }
+        if (evals >= rules.max_evals) { o.status = ST_MAXITER; break; }
       }
     }
   }
@@ -613,6 +625,16 @@ int oracle_threads(int n_threads) {
 }
 
 uint64_t oracle_splitmix64(uint64_t x) { return splitmix64(x); }
+
+// Stopping rules of the minimiser (test hook; call before a solve, not
+// during one).  Defaults: 24 accepted steps, 40 evaluations, line search
+// down to alpha = 1/16, local-minimum exit on.
+void oracle_set_rules(int32_t max_iters, int32_t max_evals, double min_alpha, int32_t localmin_exit) {
+  g_rules.max_iters = max_iters;
+  g_rules.max_evals = max_evals;
+  g_rules.min_alpha = min_alpha;
+  g_rules.localmin_exit = localmin_exit != 0;
+}
 
 // Candidate sequences (Algorithm 1, all_simple_paths; Sec. III).
 // Orders n = 1..max_order in turn.  quota[n-1] = -1: every ordered sequence of
@@ -881,6 +903,41 @@ int oracle_path_grad(const OracleScene* sc, int32_t n, const int32_t* ids, const
       }
   }
   return 0;
+}
+
+// oracle_path_grad over many paths (threads over paths): path i is candidate
+// cand[i] (entry cand / n_pairs, pair cand % n_pairs) with packed parameters
+// T[i][8]; it writes the upstream-weighted gradient
+//   w[i][j] = g_len[i] dL/dtheta_j + sum_r g_pts[i][r] dX_r/dtheta_j
+// for theta = (TX[3], RX[3], d_1..d_n), j < 6 + n (the rest of the row 0).
+// g_pts may be null.  Returns the number of paths whose normal matrix was
+// singular (their row is left 0).
+int oracle_path_grad_many(const OracleScene* sc, int64_t n_paths, const int32_t* ent_order,
+                          const int32_t* ent_ids, int64_t n_pairs, const int64_t* cand, const double* Tp,
+                          const double* g_len, const double* g_pts, double* w, int n_threads) {
+  std::atomic<int> bad{0};
+  parallel_for(n_paths, n_threads, [&](int64_t i) {
+    const int64_t e = cand[i] / n_pairs, p = cand[i] % n_pairs;
+    const int n = ent_order[e];
+    const int32_t* ids = ent_ids + 4 * e;
+    const double *a, *b;
+    pair_points(*sc, p, &a, &b);
+    double dL[6 + MAXN], dX[3 * MAXN * (6 + MAXN)];
+    double* wi = w + (6 + MAXN) * i;
+    for (int j = 0; j < 6 + MAXN; ++j) wi[j] = 0.0;
+    if (oracle_path_grad(sc, n, ids, a, b, Tp + 8 * i, dL, dX) != 0) {
+      ++bad;
+      return;
+    }
+    const int nt = 6 + n;
+    for (int j = 0; j < nt; ++j) {
+      double acc = g_len[i] * dL[j];
+      if (g_pts)
+        for (int r = 0; r < 3 * n; ++r) acc += g_pts[12 * i + r] * dX[r * nt + j];
+      wi[j] = acc;
+    }
+  });
+  return bad.load();
 }
 
 // Residual and points of one path at parameters T (for tests of the oracle).

@@ -714,3 +714,28 @@ def test_collapsed_segments_are_not_paths():
     assert sc.obj_kind[0] == S.PLANE and sc.obj_kind[49] == S.LINE_EDGE
     sol, ver = solve_one(sc, [0, 49])
     assert ver.valid.sum() == 0
+
+
+def test_batched_gradient_sums_equal_per_path_gradients():
+    """oracle.grad_sums (threads over paths) adds up exactly what
+    oracle.path_grad gives path by path, with length and point weights."""
+    sc = S.urban_block(2)
+    table = oracle.enumerate_sequences(sc, 2, FULL2)
+    sol, ver = oracle.candidate_range(sc, table, 0, len(table) * sc.n_pairs)
+    v = np.nonzero(ver.valid)[0]
+    assert len(v) > 50
+    rng = np.random.default_rng(0)
+    gl = rng.uniform(0.5, 1.5, len(v))
+    gp = rng.normal(size=(len(v), 12))
+    gtx, grx, gobj = oracle.grad_sums(sc, table, v, sol.T[v], gl, gp)
+    wtx, wrx, wobj = np.zeros_like(sc.tx), np.zeros_like(sc.rx), np.zeros(sc.n_obj)
+    for j, c in enumerate(v):
+        e, p = divmod(int(c), sc.n_pairs)
+        ids = table.ids[e][:table.order[e]]
+        dL, dX = oracle.path_grad(sc, ids, *sc.pair_points(p), sol.T[c])
+        w = gl[j] * dL + gp[j, :3 * len(ids)] @ dX
+        wtx[p // sc.rx.shape[0]] += w[:3]
+        wrx[p % sc.rx.shape[0]] += w[3:6]
+        for kk, o in enumerate(ids):
+            wobj[o] += w[6 + kk]
+    assert np.abs(gtx - wtx).max() < 1e-9 and np.abs(grx - wrx).max() < 1e-9 and np.abs(gobj - wobj).max() < 1e-9
