@@ -29,7 +29,12 @@
  *     argument returns MPT_ERR_ARG and enqueues nothing.  A CUDA launch or
  *     allocation failure returns MPT_ERR_CUDA.
  *   - One mpt_ctx per device and thread of control: calls that share a ctx
- *     must be issued from one host thread at a time.
+ *     must be issued from one host thread at a time, and in order on one
+ *     stream (or on streams the caller orders with events).  The context's
+ *     scratch (work-stealing counters, refine lists, validation scratch) is
+ *     reused by every call and regrown stream-ordered on the calling stream,
+ *     so two calls of one ctx that overlap on the GPU race on it.  Use one
+ *     ctx per concurrent stream.
  */
 #ifndef MPT_H_
 #define MPT_H_
@@ -80,8 +85,10 @@ enum {
   MPT_FP32 = 1,             /* FP32 iterations only, no refinement */
   MPT_FP32_FP64REFINE = 2   /* FP32 iterations, then refinement of candidates
                                that pass the FP32 cost/bounds/visibility
-                               prescreen in float-float arithmetic (48-bit
-                               significand), stored as FP64 */
+                               prescreen in float-float arithmetic (pairs of
+                               FP32, 48-bit significand; not FP64 arithmetic),
+                               results stored as FP64; acceptance decisions
+                               near their margins in FP64 */
 };
 
 /* Per-candidate termination status (low 4 bits) and flags. */
@@ -124,11 +131,18 @@ typedef struct {
 
 /* Which sequences to enumerate.  quota[n-1] for order n: -1 = every ordered
  * sequence of n distinct objects (lexicographic order of the ids), 0 = none,
- * q > 0 = q sequences drawn with SplitMix64 from `seed` (slot rule in the
- * design notes).  Sequences containing a paraboloid or an arc are repeated
- * `starts_curved` times with start index 0..starts_curved-1.  For orders
- * >= 3, every `force_edges_every`-th drawn slot places two consecutive edges
- * (0 = never). */
+ * q > 0 = q sequences drawn with SplitMix64 (Steele, Lea, Flood 2014) from
+ * `seed`, slot sl = 0..q-1 in turn.  Draw k of slot sl of order n is
+ * h_k = SplitMix64(seed ^ (n << 56 | sl << 16 | k)), k counting from 0 over
+ * the slot's draws.  Positions are filled left to right; each takes the
+ * (h_k mod r)-th object, in id order, among the r objects not taken yet in
+ * this slot.  For orders >= 3, when force_edges_every > 0, sl is a multiple of
+ * it and the scene has at least two edges, the slot first places two
+ * consecutive edges at position h_100 mod (n - 1): each is the (h_k mod r)-th
+ * edge, in id order, of the r edges not taken yet (k = 0, 1); the remaining
+ * positions then continue the draws from k = 2.  Sequences containing a
+ * paraboloid or an arc are repeated `starts_curved` times with start index
+ * 0..starts_curved-1. */
 typedef struct {
   int64_t quota[MPT_MAX_ORDER];
   uint64_t seed;
@@ -280,7 +294,9 @@ int mpt_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
  *     requests return MPT_ERR_CAPACITY before anything is enqueued;
  *   - the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device made current for the lookup);
- *     make that first call before any stream capture;
+ *     make that first call before any stream capture.  The address is kept
+ *     for the life of the process: after cudaDeviceReset on that device it
+ *     is stale, so do not call this entry point again in that process;
  *   - the call allocates nothing (no cudaMalloc, cudaFree or allocating
  *     library routine);
  *   - every call uses the same array, which keeps the previous call's

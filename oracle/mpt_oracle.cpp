@@ -27,9 +27,33 @@
 //   gradients      implicit-function theorem at the converged path (not in the
 //                  paper; built on Eq. 15)
 //
-// Readings where the paper is silent are fixed identically in the CUDA path
-// and listed with the design notes: parametrisations, threshold tau, minimum
-// segment length, initial guess, multi-start rule, visibility tolerances.
+// Readings where the paper is silent (the CUDA path fixes the same ones in
+// its own code):
+//   parametrisations  plane O + s U_ax + t V_ax; paraboloid
+//                  t0 + R (s, t, (s^2 + t^2)/(4f)); line P + t e; arc
+//                  C + Rc (cos t u + sin t (a x u)); the normal of Eq. 2 and
+//                  the tangent of Eq. 4 follow from them (signs irrelevant)
+//   threshold      tau = 1e-20 on the dimensionless cost of Eq. 15
+//   degenerate     a path with a segment shorter than 1e-5 S is rejected
+//                  (S = scene scale); a parameter beyond 1e3 S diverged
+//   initial guess  start 0: interaction k (from 0) takes the parameters of
+//                  the projection of TX if 2k < n, of RX otherwise; starts
+//                  j > 0 draw curved objects uniformly over their disc area
+//                  or angle range (SplitMix64 of pair, packed ids, start)
+//   multi-start    sequences with a paraboloid or an arc edge are solved from
+//                  the enumeration's starts_curved starts; every distinct
+//                  valid root is a path (Sec. III-B)
+//   bounds         inclusive parameter ranges ([0,U]x[0,V], disc, [t0,t1],
+//                  arc angle modulo 2 pi)
+//   visibility     a rectangle blocks a segment whose ends are both more than
+//                  1e-6 m off its plane on opposite sides with the crossing
+//                  inside it; a paraboloid patch blocks when the segment
+//                  meets it more than 1e-6 m from both ends inside its disc;
+//                  edges never block; every occluder is tested
+//   ambiguity      decisions within their tolerance bands (cost within a
+//                  factor 100 of tau, a segment within a factor 3 of the
+//                  minimum length, 1e-6 m of a bound or of an occluder's
+//                  boundary) are flagged, not compared
 // Parity unpinned: completeness of multi-root solution sets for curved
 // sequences of order >= 2 (only multi-start agreement is available).
 #include <algorithm>
@@ -640,8 +664,12 @@ void oracle_set_rules(int32_t max_iters, int32_t max_evals, double min_alpha, in
 // Orders n = 1..max_order in turn.  quota[n-1] = -1: every ordered sequence of
 // n distinct objects in lexicographic order of the ids, kept only if every
 // consecutive pair (a, b) has adj[a*n_obj + b] != 0 when adj is given;
-// quota = q > 0: q sequences drawn with SplitMix64 (slot rule in the design
-// notes).  Each sequence that contains a paraboloid or an arc is emitted
+// quota = q > 0: q sequences, slot sl = 0..q-1, whose draw k is
+// SplitMix64(seed ^ (n << 56 | sl << 16 | k)); positions left to right take
+// the (draw mod r)-th of the r objects not taken yet (in id order); every
+// force_edges_every-th slot of order >= 3 first puts two consecutive edges
+// (the (draw mod r)-th untaken edge, draws 0 and 1) at position
+// draw_100 mod (n - 1).  Each sequence that contains a paraboloid or an arc is emitted
 // `starts_curved` times (start index 0..starts_curved-1), others once.
 // Returns the number of entries; writes at most `cap` of them.
 int64_t oracle_enumerate(int32_t n_obj, const int32_t* obj_kind, int32_t max_order,

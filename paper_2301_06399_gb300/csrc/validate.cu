@@ -662,7 +662,11 @@ int launch_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* e
   const int64_t cap = cand->capacity;
   if (cap > MAX_CANDIDATES) return MPT_ERR_CAPACITY;
   const int64_t n_groups = (cap + GROUP - 1) / GROUP;
-  if (n_groups < 1) return MPT_OK;
+  if (n_groups < 1) {
+    // no candidate to list: the count is still written
+    MPT_CUDA_TRY(cudaMemsetAsync(d_valid_count, 0, sizeof(int64_t), st));
+    return MPT_OK;
+  }
   // a list as long as the candidates: it never overflows
   const size_t need = val_bytes(n_groups, cap);
   if (ctx->vscratch_bytes < need) {
@@ -722,7 +726,11 @@ static int launch_validate_noalloc(mpt_ctx* ctx, const mpt_scene* scene, const m
   const int64_t cap = cand->capacity;
   if (cap > NOALLOC_MAX_CANDIDATES) return MPT_ERR_CAPACITY;
   const int64_t n_groups = (cap + GROUP - 1) / GROUP;
-  if (n_groups < 1) return MPT_OK;
+  if (n_groups < 1) {
+    // no candidate to list: the count is still written
+    MPT_CUDA_TRY(cudaMemsetAsync(d_valid_count, 0, sizeof(int64_t), st));
+    return MPT_OK;
+  }
   unsigned char* base = nullptr;
   const int rc = noalloc_scratch(ctx->device, &base);
   if (rc != MPT_OK) return rc;

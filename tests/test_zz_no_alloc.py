@@ -100,3 +100,59 @@ def test_noalloc_groups_beyond_its_list_match_validate(mpt):
     assert torch.equal(got.X[:, :n], want.X[:, :n])
     assert torch.equal(got.length[:n], want.length[:n])
     assert ctx.check() == mpt.MPT_OK
+
+
+def test_noalloc_call_leaves_free_device_memory_unchanged(mpt):
+    """The property the entry point exists for.  A fresh context (its own
+    validation scratch never grown) takes a small warm-up call (the first call
+    on a device looks up the array's address), then calls on a thousand times
+    more candidates: an allocation sized by the input would have to grow
+    there, yet the device's free memory is the same before and after."""
+    ctx = mpt.Context(0)
+    stream = torch.cuda.current_stream()
+    small = S.street_canyon()
+    ds_s = mpt.DeviceScene(ctx, small)
+    c_s = mpt.enumerate_candidates(ds_s, 2, S.CONFIG_SPECS["street_canyon"])
+    s_s = mpt.solve(ds_s, c_s, mpt.FP32_FP64REFINE)
+    p_s = mpt.alloc_paths(c_s.capacity, ds_s.tx.device)
+    big = S.urban_block(8)
+    ds_b = mpt.DeviceScene(ctx, big)
+    c_b = mpt.enumerate_candidates(ds_b, 2, S.CONFIG_SPECS["urban_block"])
+    s_b = mpt.solve(ds_b, c_b, mpt.FP32_FP64REFINE)
+    p_b = mpt.alloc_paths(c_b.capacity, ds_b.tx.device)
+    assert _call_noalloc(mpt, ds_s, c_s, s_s, p_s, stream) == mpt.MPT_OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert _call_noalloc(mpt, ds_b, c_b, s_b, p_b, stream) == mpt.MPT_OK
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, (free0, free1)
+    assert p_b.n() > 1000 and ctx.check() == mpt.MPT_OK
+    # for contrast (reported): the allocating entry point grows the fresh
+    # context's scratch for the same input
+    mpt.validate(ds_b, c_b, s_b, out=p_b)
+    torch.cuda.synchronize()
+    print(f"free device memory: {free0} before and {free1} after three no-allocation calls; "
+          f"{torch.cuda.mem_get_info()[0]} after one mpt_validate")
+
+
+@pytest.mark.parametrize("which", ["mpt_validate", "mpt_validate_noalloc"])
+def test_zero_capacity_candidate_list_writes_a_zero_count(mpt, which):
+    ctx = mpt.Context(0)
+    sc = S.street_canyon()
+    ds = mpt.DeviceScene(ctx, sc)
+    cands = mpt.enumerate_candidates(ds, 2, S.CONFIG_SPECS["street_canyon"])
+    sols = mpt.solve(ds, cands, mpt.FP32_FP64REFINE)
+    paths = mpt.alloc_paths(4, ds.tx.device)
+    paths.count.fill_(77)
+    torch.cuda.synchronize()
+    cands.capacity = 0  # an empty candidate buffer
+    ep, cs, ss, ps = ds.endpoints(), cands.struct(), sols.struct(), paths.struct()
+    fn = getattr(mpt.lib(), which)
+    stream = torch.cuda.current_stream()
+    rc = fn(ds.ctx.h, ds.h, C.byref(ep), C.byref(cs), C.byref(ss), C.c_double(mpt.TAU), C.byref(ps),
+            C.c_void_p(paths.count.data_ptr()), C.c_void_p(stream.cuda_stream))
+    torch.cuda.synchronize()
+    assert rc == mpt.MPT_OK
+    assert int(paths.count.item()) == 0
