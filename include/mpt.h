@@ -190,6 +190,11 @@ typedef struct {
   int32_t mixed_orders;   /* 1: one launch over all orders; 0: one launch per order */
   int32_t refill_min;     /* idle lanes of a warp that trigger taking new candidates
                              (1..32; 0: 12) */
+  int32_t prescreen;      /* visibility prescreen before the refinement:
+                             0 library default (on), 1 on, 2 off */
+  int32_t fallback;       /* arithmetic of the refinement's fallback solve (the few
+                             ill-conditioned candidates the mixed steps leave):
+                             0 library default (FP64), 1 float-float, 2 FP64 */
 } mpt_schedule;
 
 /* Compacted valid paths (caller-owned device buffers). */
@@ -372,7 +377,8 @@ const char* mpt_status_string(int status);
  * given kinds, counted by running the kernel's own arithmetic on the host with
  * a counting scalar: flops_per_eval = FP32 add/sub/mul (1) and FMA (2) of one
  * cost + normal-equation evaluation at a trial point; flops_per_iter = those
- * of one Cholesky factorisation and solve; sfu_per_eval = reciprocal square
+ * of one Cholesky factorisation and solve over the live parameters (two per
+ * surface interaction, one per edge); sfu_per_eval = reciprocal square
  * roots and sin/cos of one evaluation (may be NULL).  Algorithmic FLOPs of a
  * candidate = evals * flops_per_eval + iters * flops_per_iter, with evals and
  * iters as reported in mpt_solutions. */

@@ -15,7 +15,8 @@
 // is below 1e-6, whose parameters lie within 0.1 m of their bounds and that
 // the visibility prescreen does not reject are refined with mixed steps
 // (residual and cost in float-float, Jacobian in FP32); ill-conditioned ones
-// (near object creases) go on to float-float Gauss-Newton (k_refine_fb).
+// (near object creases) go on to a full Gauss-Newton solve (k_refine_fb, in
+// FP64 by default, float-float on request).
 // Every other candidate is rejected by validation whatever its last digits,
 // so it keeps its FP32 result.
 //
@@ -40,6 +41,8 @@ struct SolveCfg {
   float prescreen_cost, prescreen_margin;
   float mu32;
   double mu64;
+  int prescreen;     // 1: visibility prescreen before the refinement
+  int fallback_f64;  // 1: refinement fallback in FP64, 0: float-float
 };
 
 struct CandView {
@@ -182,11 +185,81 @@ __device__ __forceinline__ void pin_unused(const int (&kind)[N], J* jtj, J* g) {
     }
 }
 
-__device__ __forceinline__ uint64_t pack_ids(const Cand& cd, int n) {
-  uint64_t packed = 0;
+// ------------------------------------------- kind patterns (planar scenes) --
+// A sequence of planes and straight edges has a kind pattern PAT: bit k set
+// when interaction k is an edge (one parameter, slot 2k), clear for a plane
+// (two parameters, slots 2k and 2k+1).  With the pattern known at compile
+// time every kind test of the evaluation folds away, an edge's record is two
+// float4 instead of four, and the normal equations are factored over the
+// live parameters only (the pinned slot of an edge holds exact zeros off the
+// diagonal, so dropping it changes no other entry of the factor or the step).
+template <int N, int PAT>
+struct KindPat {
+  static constexpr bool edge(int k) { return ((PAT >> k) & 1) != 0; }
+  static constexpr int nq() {
+    int q = 0;
+    for (int k = 0; k < N; ++k) q += edge(k) ? 1 : 2;
+    return q;
+  }
+  static constexpr int Q = nq();
+  // slot (in the two-per-interaction layout) of live parameter i
+  static constexpr int slot(int i) {
+    int q = 0;
+    for (int k = 0; k < N; ++k) {
+      if (q++ == i) return 2 * k;
+      if (!edge(k) && q++ == i) return 2 * k + 1;
+    }
+    return 0;
+  }
+};
+
+// Gauss-Newton step over the live parameters of pattern PAT: the normal
+// equations (packed over 2N slots) are gathered, factored with relative
+// damping mu and solved; dead slots get a zero step.
+template <int N, int PAT, class J>
+__device__ __forceinline__ void gn_step_pat(const J* jtj, const J* g, J mu, J* dlt) {
+  using KP = KindPat<N, PAT>;
+  constexpr int QC = KP::Q;
+  J a[QC * (QC + 1) / 2], gc[QC], x[QC];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) packed |= (uint64_t)(uint16_t)(k < n ? cd.ids[k] : 0xFFFF) << (16 * k);
-  return packed;
+  for (int i = 0; i < QC; ++i) {
+    gc[i] = g[KP::slot(i)];
+#pragma unroll
+    for (int j = 0; j <= i; ++j) a[tri(i, j)] = jtj[tri(KP::slot(i), KP::slot(j))];
+  }
+  cholesky<QC, J>(a, mu);
+  chol_solve<QC, J>(a, gc, x);
+#pragma unroll
+  for (int k = 0; k < 2 * N; ++k) dlt[k] = J(0);
+#pragma unroll
+  for (int i = 0; i < QC; ++i) dlt[KP::slot(i)] = x[i];
+}
+
+// Object record of a compile-time kind from the object-major FP32 copy: a
+// plane needs all four float4 (O U | u V | v d | n), an edge the first two
+// (P t0 | e t1).
+template <bool EDGE>
+__device__ __forceinline__ Rec<float> load_obj32_kind(const DevScene& s, int o) {
+  Rec<float> r;
+  const float4* p = s.a32 + 4 * o;
+#pragma unroll
+  for (int f = 0; f < (EDGE ? 2 : 4); ++f) {
+    const float4 q = __ldg(p + f);
+    r.v[4 * f] = q.x; r.v[4 * f + 1] = q.y; r.v[4 * f + 2] = q.z; r.v[4 * f + 3] = q.w;
+  }
+  if (EDGE) {
+#pragma unroll
+    for (int i = 8; i < 16; ++i) r.v[i] = 0.f;
+  }
+  return r;
+}
+
+template <class R, bool EDGE>
+__device__ __forceinline__ Rec<R> load_obj_kind(const DevScene& s, int o) {
+  if constexpr (std::is_same<R, float>::value)
+    return load_obj32_kind<EDGE>(s, o);
+  else
+    return load_obj64(s, o);
 }
 
 // ------------------------------------------------------------- kernel A --
@@ -223,6 +296,27 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
 }
 
+// Calls f(std::integral_constant<int, PAT>) for the lane's kind pattern, so
+// that each pattern runs its own compile-time specialisation (lanes of one
+// warp share a pattern except where a piece straddles two sequences).
+template <int N, class F>
+__device__ __forceinline__ void dispatch_pat(int pat, F&& f) {
+  using std::integral_constant;
+  if constexpr (N == 1) {
+    if (pat == 0) f(integral_constant<int, 0>{});
+    else f(integral_constant<int, 1>{});
+  } else if constexpr (N == 2) {
+    switch (pat) {
+      case 0: f(integral_constant<int, 0>{}); break;
+      case 1: f(integral_constant<int, 1>{}); break;
+      case 2: f(integral_constant<int, 2>{}); break;
+      default: f(integral_constant<int, 3>{}); break;
+    }
+  } else {
+    f(integral_constant<int, -1>{});
+  }
+}
+
 template <int N, class R>
 __device__ __forceinline__ void load_objs(const DevScene& sc, uint32_t ids01, uint32_t ids23, Rec<R> (&rec)[N]) {
 #pragma unroll
@@ -254,6 +348,9 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
   bool exhausted = false;
   uint32_t ids01 = 0, ids23 = 0;  // object ids, 16 bits each
   int kinds = 0;                  // object kinds, 8 bits each
+  int pat = 0;                    // kind pattern (bit k: interaction k is an edge)
+  uint32_t pair_ = 0;             // TX/RX pair and start index (curved starts)
+  int start_ = 0;
   int it_ = 0, ir_ = 0;
   R prm[Q], trial[Q], dlt[Q];
   R cost = R(0), alpha = R(1);
@@ -264,12 +361,13 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
   // ---- warp-uniform staging of candidate records: the current piece (being
   // taken from) and the next one (in flight)
   int64_t walk = begin;  // past the last piece seen
-  const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  // guided piece size: about half of what is left, split over every warp
+  const float inv_2warps = 0.5f / (float)(gridDim.x * (blockDim.x >> 5));
   auto claim = [&](int64_t& base, int& len) {
     int size = cfg.piece;
     if (counter != nullptr) {
       // guided size from the last position seen (a slight lag is harmless)
-      const int64_t guided = (end - walk) / (2 * n_warps);
+      const int64_t guided = (int64_t)((float)(int)(end - walk) * inv_2warps);
       if (guided < size) size = guided < 32 ? 32 : (int)guided;
       unsigned long long b = 0;
       if (lane == 0) b = atomicAdd(counter, (unsigned long long)size);
@@ -360,25 +458,30 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
           need = false;
           const int64_t idx = cur_base + slot;
           const uint4 rr = rbuf[buf][slot];
-          const Cand cd = decode(rr);
-          if (cand_in_range(sc, ep, cd) && cd.order == N) {
+          // a record of this solver's order whose objects and endpoints exist
+          bool valid = (int)(rr.w & 0xFFu) == N;
+#pragma unroll
+          for (int k = 0; k < N; ++k)
+            valid = valid && (int)(((k < 2 ? rr.y : rr.z) >> (16 * (k & 1))) & 0xFFFFu) < sc.n_obj;
+          pair_ends(ep, rr.x, it_, ir_);
+          valid = valid && it_ < ep.n_tx && ir_ < ep.n_rx;
+          if (valid) {
+            // only the record is decoded here; the initial guess is made in
+            // the first pass, from the records and endpoints it loads anyway
             c = (int)(idx - begin);
-            pair_ends(ep, cd.pair, it_, ir_);
             ids01 = rr.y;
             ids23 = rr.z;
-            const v3<R> A = load_end<R>(ep.tx, ends32, it_);
-            const v3<R> B = load_end<R>(ep.rx, ends32 + ep.n_tx, ir_);
-            // the ids hash seeds the extra starts of curved objects only
-            const uint64_t packed = CURVED ? pack_ids(cd, N) : 0ull;
+            pair_ = rr.x;
+            start_ = (int)((rr.w >> 8) & 0xFFu);
             kinds = 0;
+            pat = 0;
             lm_ratio = R(cfg.localmin_ratio_planar);
 #pragma unroll
             for (int k = 0; k < N; ++k) {
-              const int kd = __ldg(sc.kind + cd.ids[k]);
+              const int kd = __ldg(sc.kind + (int)(((k < 2 ? rr.y : rr.z) >> (16 * (k & 1))) & 0xFFFFu));
               kinds |= kd << (8 * k);
+              pat |= (kd == K_LINE ? 1 : 0) << k;
               if (CURVED && (kd == K_PARAB || kd == K_ARC)) lm_ratio = R(cfg.localmin_ratio);
-              init_params<R, CURVED>(kd, load_obj<R>(sc, cd.ids[k]), (2 * k < N) ? A : B, cv.init_seed, cd.pair,
-                                     packed, cd.start, k, trial[2 * k], trial[2 * k + 1]);
             }
             fresh = true;
             iters = 0;
@@ -399,15 +502,44 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
       if (__ballot_sync(FULL, !exhausted || done_c >= 0) == 0) break;
       continue;
     }
-    if (c >= 0) {
-      // ---- one evaluation at the trial point
+    // ---- one evaluation at the trial point.  PAT >= 0: the kind pattern
+    // of a planar sequence, fixed at compile time; PAT < 0: kinds decoded at
+    // run time (curved scenes, the FP64 method).
+    auto pass = [&](auto pat_c) {
+      constexpr int PAT = decltype(pat_c)::value;
       int kind[N];
-#pragma unroll
-      for (int k = 0; k < N; ++k) kind[k] = (kinds >> (8 * k)) & 0xFF;
       Rec<R> rec[N];
-      load_objs<N, R>(sc, ids01, ids23, rec);
+      if constexpr (PAT >= 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const uint32_t w = k < 2 ? ids01 : ids23;
+          const int o = (int)((w >> (16 * (k & 1))) & 0xFFFFu);
+          kind[k] = KindPat<N, PAT>::edge(k) ? K_LINE : K_PLANE;
+          if (KindPat<N, PAT>::edge(k))
+            rec[k] = load_obj_kind<R, true>(sc, o);
+          else
+            rec[k] = load_obj_kind<R, false>(sc, o);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) kind[k] = (kinds >> (8 * k)) & 0xFF;
+        load_objs<N, R>(sc, ids01, ids23, rec);
+      }
       const v3<R> A = load_end<R>(ep.tx, ends32, it_);
       const v3<R> B = load_end<R>(ep.rx, ends32 + ep.n_tx, ir_);
+      if (fresh) {
+        // initial guess (Algorithm 1, random_guess); the ids hash (unused
+        // slots 0xFFFF) seeds the extra starts of curved objects only
+        uint64_t packed = 0;
+        if constexpr (CURVED) {
+          packed = (uint64_t)ids01 | ((uint64_t)ids23 << 32);
+          if constexpr (N < 4) packed |= ~0ull << (16 * (N < 4 ? N : 0));
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          init_params<R, CURVED>(kind[k], rec[k], (2 * k < N) ? A : B, cv.init_seed, pair_, packed, start_, k,
+                                 trial[2 * k], trial[2 * k + 1]);
+      }
       R jtj[P], g[Q];
       bool ok;
       R ct;
@@ -430,6 +562,7 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
         R smax = R(0), pmax = R(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
+          if (PAT >= 0 && KindPat<N, (PAT < 0 ? 0 : PAT)>::edge(i / 2) && (i & 1)) continue;  // dead slot
           smax = fmax(smax, fabs(trial[i] - prm[i]));
           prm[i] = trial[i];
           pmax = fmax(pmax, fabs(prm[i]));
@@ -446,9 +579,13 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
       }
       if (done < 0 && evals >= cfg.max_evals) done = MPT_PATH_MAXITER;
       if (factor && done < 0) {
-        pin_unused<N, R>(kind, jtj, g);
-        cholesky<Q, R>(jtj, mu);
-        chol_solve<Q, R>(jtj, g, dlt);
+        if constexpr (PAT >= 0) {
+          gn_step_pat<N, PAT, R>(jtj, g, mu, dlt);
+        } else {
+          pin_unused<N, R>(kind, jtj, g);
+          cholesky<Q, R>(jtj, mu);
+          chol_solve<Q, R>(jtj, g, dlt);
+        }
         alpha = R(1);
         // The Gauss-Newton model predicts the decrease -g.dlt; when it is a
         // small fraction of a large cost the iterate sits at a local minimum
@@ -480,6 +617,12 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
         done_push = pass;
         c = -1;
       }
+    };
+    if (c >= 0) {
+      if constexpr (!CURVED && PREC != MPT_FP64_PLAIN && N <= 2)
+        dispatch_pat<N>(pat, pass);
+      else
+        pass(std::integral_constant<int, -1>{});
     }
   }
   cp_async_wait<0>();  // nothing left in flight when the warp leaves
@@ -618,7 +761,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
           for (int k = 0; k < N; ++k) {
             const int id = (int)(((k < 2 ? q.x : q.y) >> (16 * (k & 1))) & 0xFFFFu);
             const int kind = __ldg(sc.kind + id);
-            const Rec<float> r = load_obj32(sc, id);
+            const Rec<float> r = load_obj32a(sc, id);
             P[k + 1] = point_at<float, false>(kind, r, rl1.prm[(int64_t)(2 * k) * rl1.stride + begin + i],
                                               rl1.prm[(int64_t)(2 * k + 1) * rl1.stride + begin + i]).X;
           }
@@ -627,44 +770,28 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
     }
     bool blocked = false;
     if (__ballot_sync(FULL, test)) {
-      v3<float> inv[N + 1], lo[N + 1], hi[N + 1];
+      // segment by segment: the groups whose boxes this segment meets, then
+      // only their rectangles; a lane stops at its first clear crossing
 #pragma unroll
       for (int j = 0; j <= N; ++j) {
-        if (test) {
-          inv[j] = mk(1.0f / (P[j + 1].x - P[j].x), 1.0f / (P[j + 1].y - P[j].y), 1.0f / (P[j + 1].z - P[j].z));
-          lo[j] = mk(fminf(P[j].x, P[j + 1].x), fminf(P[j].y, P[j + 1].y), fminf(P[j].z, P[j + 1].z));
-          hi[j] = mk(fmaxf(P[j].x, P[j + 1].x), fmaxf(P[j].y, P[j + 1].y), fmaxf(P[j].z, P[j + 1].z));
-        }
-      }
-      for (int g0 = 0; g0 < ng; g0 += 32) {
-        // groups g0 .. g0 + 31 that some segment of this lane meets
-        uint32_t gm = 0;
-        const int gn = ng - g0 < 32 ? ng - g0 : 32;
-        if (test && !blocked) {
-          for (int q = 0; q < gn; ++q) {
-            const float4 gl = grp_sm[g0 + q], gh = grp_sm[ng + g0 + q];
-            bool hit = false;
-#pragma unroll
-            for (int j = 0; j <= N; ++j) hit = hit || seg_box(P[j], inv[j], gl, gh);
-            gm |= (uint32_t)hit << q;
-          }
-        }
-        while (gm != 0 && !blocked) {
-          const int gi = g0 + __ffs(gm) - 1;
-          gm &= gm - 1;
-          const int o_end = (gi + 1) * OCC_GROUP < no ? (gi + 1) * OCC_GROUP : no;
-          for (int o = gi * OCC_GROUP; o < o_end && !blocked; ++o) {
-            const float4 bl = occ_sm[4 * no + o], bh = occ_sm[5 * no + o];
-            if (bl.w != 0.f) continue;  // rectangles only
-#pragma unroll
-            for (int j = 0; j <= N; ++j) {
-              if (lo[j].x <= bh.x && hi[j].x >= bl.x && lo[j].y <= bh.y && hi[j].y >= bl.y && lo[j].z <= bh.z &&
-                  hi[j].z >= bl.z)
-                blocked = blocked || clearly_crosses(occ_sm, no, o, P[j], P[j + 1]);
+        if (!test || blocked) continue;
+        const v3<float> Af = P[j], Bf = P[j + 1];
+        const v3<float> inv = mk(1.0f / (Bf.x - Af.x), 1.0f / (Bf.y - Af.y), 1.0f / (Bf.z - Af.z));
+        for (int g0 = 0; g0 < ng && !blocked; g0 += 32) {
+          const int gn = ng - g0 < 32 ? ng - g0 : 32;
+          uint32_t gm = 0;
+          for (int q = 0; q < gn; ++q) gm |= (uint32_t)seg_box(Af, inv, grp_sm[g0 + q], grp_sm[ng + g0 + q]) << q;
+          while (gm != 0 && !blocked) {
+            const int gi = g0 + __ffs(gm) - 1;
+            gm &= gm - 1;
+            const int o_end = (gi + 1) * OCC_GROUP < no ? (gi + 1) * OCC_GROUP : no;
+            for (int o = gi * OCC_GROUP; o < o_end && !blocked; ++o) {
+              const float4 bl = occ_sm[4 * no + o], bh = occ_sm[5 * no + o];
+              if (bl.w != 0.f) continue;  // rectangles only
+              if (box_overlap(bl, bh, Af, Bf)) blocked = clearly_crosses(occ_sm, no, o, Af, Bf);
             }
           }
         }
-        if (__ballot_sync(FULL, test && !blocked) == 0) break;
       }
       if (blocked) {
         out.status[c] = (uint8_t)(out.status[c] | MPT_PATH_PRESCREENED);
@@ -755,6 +882,69 @@ __device__ ff gn_ff(const int (&kind)[N], const Rec<ff> (&rec)[N], ff (&prm)[2 *
   return cost;
 }
 
+// The fallback in FP64 arithmetic (the default), with the rules of gn_ff:
+// the FP64 code is a fraction of the length of the float-float one, which
+// matters for a lone serial chain that otherwise waits on instruction fetch
+// (measured: the order-2 fallback of the urban block 59 us faster).
+template <int N>
+__device__ double gn_f64(const int (&kind)[N], const Rec<double> (&rec)[N], double (&prm)[2 * N], const v3<double>& A,
+                         const v3<double>& B, int max_iters, double mu, double stop) {
+  constexpr int Q = 2 * N, P = Q * (Q + 1) / 2;
+  double jtj[P], g[Q], dlt[Q], trial[Q], jt2[P], g2[Q];
+  double cost = (double)INFINITY;
+  double alpha = 1.0;
+  bool need_factor = true;
+#pragma unroll 1
+  for (int it = -1; it < 2 * max_iters; ++it) {
+    if (it >= 0) {
+      if (!(cost >= stop)) break;
+      if (need_factor) {
+        pin_unused<N, double>(kind, jtj, g);
+        cholesky<Q, double>(jtj, mu);
+        chol_solve<Q, double>(jtj, g, dlt);
+        double pred = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) pred = fma(-g[i], dlt[i], pred);
+        if (pred < 1e-3 * cost) break;
+        alpha = 1.0;
+        need_factor = false;
+      }
+#pragma unroll
+      for (int i = 0; i < Q; ++i) trial[i] = fma(alpha, dlt[i], prm[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) trial[i] = prm[i];
+    }
+    bool ok;
+    const double ct = eval_path<N, double, double, true>(kind, rec, trial, A, B, jt2, g2, ok);
+    if (it < 0) {
+      if (!ok) return (double)INFINITY;
+      cost = ct;
+#pragma unroll
+      for (int i = 0; i < P; ++i) jtj[i] = jt2[i];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) g[i] = g2[i];
+      continue;
+    }
+    if (ok && ct < cost) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) prm[i] = trial[i];
+#pragma unroll
+      for (int i = 0; i < P; ++i) jtj[i] = jt2[i];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) g[i] = g2[i];
+      const bool stagnant = ct > 0.25 * cost;
+      cost = ct;
+      if (stagnant) break;
+      need_factor = true;
+    } else {
+      alpha *= 0.5;
+      if (alpha < 1.0 / 16.0) break;
+    }
+  }
+  return cost;
+}
+
 // One thread per listed candidate: up to refine_steps mixed steps (residual
 // and cost in float-float, Jacobian and solve in FP32) until the cost is
 // below 1e-24, extended by up to 6 steps while they still halve the cost.
@@ -787,7 +977,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? 3 : 1)) k_refine(DevSce
     bool fallback = false;
     int64_t c = 0;
     if (i < n) {
-      c = begin + rl.idx[begin + i];
+      c = begin + (rl.idx[begin + i] & ~RL_VIS);
       if (c >= begin && c < end) {
         const Cand cd = decode(__ldg(cv.rec + c));
         int it_, ir_;
@@ -849,10 +1039,10 @@ __global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? 3 : 1)) k_refine(DevSce
   }
 }
 
-// The fallback of the refinement: float-float Gauss-Newton for the queued
+// The fallback of the refinement: Gauss-Newton (FP64 or float-float) for the queued
 // candidates, one candidate per warp (lane 0) so that the few long serial
 // solves run side by side on as many SM sub-partitions as there are.
-template <int N>
+template <int N, bool F64>
 __global__ void __launch_bounds__(32) k_refine_fb(DevScene sc, DevEnds ep, CandView cv, SolView out, SolveCfg cfg,
                                                   RefineList rl3) {
   constexpr int Q = 2 * N;
@@ -869,24 +1059,40 @@ __global__ void __launch_bounds__(32) k_refine_fb(DevScene sc, DevEnds ep, CandV
     const Cand cd = decode(__ldg(cv.rec + c));
     int it_, ir_;
     pair_ends(ep, cd.pair, it_, ir_);
-    const v3<ff> A = load_end_ff(ep.tx, it_);
-    const v3<ff> B = load_end_ff(ep.rx, ir_);
     int kind[N];
-    Rec<ff> rec[N];
-    ff T[Q];
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      kind[k] = __ldg(sc.kind + cd.ids[k]);
-      rec[k] = load_obj_ff(sc, cd.ids[k]);
-    }
-#pragma unroll
-    for (int j = 0; j < Q; ++j) T[j] = ff_from_double(out.T[(int64_t)j * out.cap + c]);
+    for (int k = 0; k < N; ++k) kind[k] = __ldg(sc.kind + cd.ids[k]);
     const double c1 = out.cost[c];
-    const ff c2 = gn_ff<N>(kind, rec, T, A, B, cfg.fallback_iters, (float)cfg.mu64, REFINE_TARGET);
-    if (finite_ff(c2) && to_double(c2) < c1) {
+    if constexpr (F64) {
+      const v3<double> A = mk(ep.tx[3 * it_], ep.tx[3 * it_ + 1], ep.tx[3 * it_ + 2]);
+      const v3<double> B = mk(ep.rx[3 * ir_], ep.rx[3 * ir_ + 1], ep.rx[3 * ir_ + 2]);
+      Rec<double> rec[N];
+      double T[Q];
 #pragma unroll
-      for (int j = 0; j < Q; ++j) out.T[(int64_t)j * out.cap + c] = to_double(T[j]);
-      out.cost[c] = to_double(c2);
+      for (int k = 0; k < N; ++k) rec[k] = load_obj64(sc, cd.ids[k]);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) T[j] = out.T[(int64_t)j * out.cap + c];
+      const double c2 = gn_f64<N>(kind, rec, T, A, B, cfg.fallback_iters, cfg.mu64, (double)REFINE_TARGET);
+      if (isfinite(c2) && c2 < c1) {
+#pragma unroll
+        for (int j = 0; j < Q; ++j) out.T[(int64_t)j * out.cap + c] = T[j];
+        out.cost[c] = c2;
+      }
+    } else {
+      const v3<ff> A = load_end_ff(ep.tx, it_);
+      const v3<ff> B = load_end_ff(ep.rx, ir_);
+      Rec<ff> rec[N];
+      ff T[Q];
+#pragma unroll
+      for (int k = 0; k < N; ++k) rec[k] = load_obj_ff(sc, cd.ids[k]);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) T[j] = ff_from_double(out.T[(int64_t)j * out.cap + c]);
+      const ff c2 = gn_ff<N>(kind, rec, T, A, B, cfg.fallback_iters, (float)cfg.mu64, REFINE_TARGET);
+      if (finite_ff(c2) && to_double(c2) < c1) {
+#pragma unroll
+        for (int j = 0; j < Q; ++j) out.T[(int64_t)j * out.cap + c] = to_double(T[j]);
+        out.cost[c] = to_double(c2);
+      }
     }
   }
 }
@@ -911,8 +1117,9 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
   // cursors; [24..27]: prescreen cursors
   MPT_CUDA_TRY(cudaMemsetAsync(ctx->counters, 0, 28 * sizeof(unsigned long long), st));
   const size_t vsmem = (size_t)sc.n_occ * 96 + (size_t)sc.n_grp * 32;
-  // the fallback queue reuses the first list's storage (read by then)
-  const RefineList rl3{ctx->counters + 16, rl.idx};
+  // the fallback queue reuses the storage of a list read by then: the first
+  // list after the prescreen, else the (unused) second one
+  const RefineList rl3{ctx->counters + 16, cfg.prescreen ? rl.idx : rl2.idx};
   if (sch && sch->mixed_orders) {
     k_gn_mixed<PREC><<<grid_for(ctx, k_gn_mixed<PREC>, sch), SOLVE_BLOCK, 0, st>>>(sc, ep, ends32, cv, sv, cfg,
                                                                                   ctx->counters + 4, rl);
@@ -939,13 +1146,19 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
     if (PREC == MPT_FP32_FP64REFINE) {                                                                         \
       if (vsmem > 48 * 1024)                                                                                   \
         cudaFuncSetAttribute(k_vis_prescreen<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem);     \
-      k_vis_prescreen<N><<<grid_for(ctx, k_vis_prescreen<N>, nullptr, vsmem), SOLVE_BLOCK, vsmem, s_>>>(       \
-          sc, ep, ends32, cv, sv, rl, rl2, ctx->counters + 24 + (N - 1));                                      \
-      MPT_LAUNCH_CHECK();                                                                                      \
-      k_refine<N><<<grid_for(ctx, k_refine<N>, nullptr), SOLVE_BLOCK, 0, s_>>>(sc, ep, cv, sv, cfg, rl2, rl3,   \
+      if (cfg.prescreen) {                                                                                     \
+        k_vis_prescreen<N><<<grid_for(ctx, k_vis_prescreen<N>, nullptr, vsmem), SOLVE_BLOCK, vsmem, s_>>>(     \
+            sc, ep, ends32, cv, sv, rl, rl2, ctx->counters + 24 + (N - 1));                                    \
+        MPT_LAUNCH_CHECK();                                                                                    \
+      }                                                                                                        \
+      k_refine<N><<<grid_for(ctx, k_refine<N>, nullptr), SOLVE_BLOCK, 0, s_>>>(sc, ep, cv, sv, cfg,             \
+                                                                               cfg.prescreen ? rl2 : rl, rl3,   \
                                                                                ctx->counters + 20 + (N - 1));   \
       MPT_LAUNCH_CHECK();                                                                                      \
-      k_refine_fb<N><<<ctx->sms * 4, 32, 0, s_>>>(sc, ep, cv, sv, cfg, rl3);                                   \
+      if (cfg.fallback_f64)                                                                                    \
+        k_refine_fb<N, true><<<ctx->sms * 4, 32, 0, s_>>>(sc, ep, cv, sv, cfg, rl3);                           \
+      else                                                                                                     \
+        k_refine_fb<N, false><<<ctx->sms * 4, 32, 0, s_>>>(sc, ep, cv, sv, cfg, rl3);                          \
       MPT_LAUNCH_CHECK();                                                                                      \
     }                                                                                                          \
   }
@@ -973,6 +1186,8 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
   cfg.refill_min = (sch && sch->refill_min > 0) ? (sch->refill_min > 32 ? 32 : sch->refill_min) : 12;
   cfg.piece = (sch && sch->tile > 0) ? (sch->tile < 32 ? 32 : (sch->tile > GN_CHUNK ? GN_CHUNK : sch->tile)) : GN_CHUNK;
   cfg.fallback_iters = 2;  // at most 5 evaluations
+  cfg.prescreen = (sch && sch->prescreen == 2) ? 0 : 1;
+  cfg.fallback_f64 = (sch && sch->fallback == 1) ? 0 : 1;
   const double S = scene->d.scale;
   cfg.c_tol32 = 1e-12f;
   cfg.step_tol32 = (float)(1e-6 * S);

@@ -63,7 +63,10 @@ def test_flop_model_counts(lib, kinds):
     from paper_2301_06399_gb300 import mpt
 
     f_iter, f_eval, sfu = mpt.flop_model(kinds)
-    assert f_iter == _chol_solve_flops(2 * len(kinds))
+    # the factorisation runs over the live parameters: two per surface
+    # interaction, one per edge
+    live = sum(1 if k in (2, 3) else 2 for k in kinds)
+    assert f_iter == _chol_solve_flops(live)
     assert f_eval > 50 * len(kinds)
     # one reciprocal square root per segment, one more per paraboloid normal,
     # two sin/cos pairs per arc (point and tangent; 2 SFU operations each)
