@@ -11,11 +11,19 @@ candidate solves per step, synthetic seeded scene.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Prints one JSON line (rank 0).  `value` is device-resident throughput
-(scene and endpoints already in HBM); `e2e` is the same metric through the
-C ABI starting from host arrays, with the host->device copies of the scene
-and endpoints and the device->host read of the valid paths inside the timed
-region.  Under torchrun each rank solves its own batch (weak scaling, no
-data-path collective).
+(scene and endpoints already in HBM) with the solve's schedule picked by
+mpt_autotune for this workload before the warm-up (--no-tune: library
+defaults); `e2e` is the same metric through the C ABI starting from host
+arrays, with the host->device copies of the scene and endpoints and the
+device->host read of the valid paths inside the timed region.  The default
+600 steps keep the timed region above a second.  `workloads` times the other
+workloads as their own steps, outside the timed region: the street canyon
+(plain FP64 method and FP32 + refinement), the mixed-order city (library
+defaults and autotuned, eager and as a CUDA graph), the curved scene, the
+64x64-RX block (forward alone and forward + adjoint) and the image method
+beside the minimiser on the urban block's reflection-only candidates.
+Under torchrun each rank solves its own batch (weak scaling, no data-path
+collective).
 """
 from __future__ import annotations
 
@@ -205,6 +213,121 @@ def algorithmic_flops(mpt, sc, cands, sols, n):
     return total
 
 
+def solve_launches(mpt, sch, n_orders=4) -> int:
+    """Kernels one FP32+refinement mpt_solve launches under schedule sch."""
+    mixed = bool(sch.mixed_orders)
+    prescreen = sch.prescreen != 2
+    return 1 + (1 if mixed else n_orders) + n_orders * (3 if prescreen else 2)
+
+
+def timed(stream, fn, reps, flush=None):
+    """Median device time (ms) of fn() over reps calls, CUDA events on stream,
+    an L2 flush outside the events before each call."""
+    ms = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        stream.synchronize()
+        ms.append(a.elapsed_time(b))
+    return float(np.median(ms))
+
+
+def workload_legs(mpt, ctx, dev, stream, flush, reps):
+    """The other workloads, each timed as its own step (outside the main timed
+    region): candidates/s, valid paths/s and the schedule used."""
+    from paper_2301_06399_gb300 import scenes
+
+    legs = {}
+
+    def trace_leg(sc, spec, max_order, precision=mpt.FP32_FP64REFINE, sch=None, grad_pts=False, graph=False):
+        ds = mpt.DeviceScene(ctx, sc)
+        n = mpt.candidate_count(ds, max_order, spec)
+        cands = mpt.alloc_candidates(n, dev)
+        sols = mpt.alloc_solutions(n, dev)
+        paths = mpt.alloc_paths(1 << 22, dev)
+        g_len = torch.ones(paths.capacity, dtype=torch.float64, device=dev)
+        g_pts = torch.full((12, paths.capacity), 0.1, dtype=torch.float64, device=dev) if grad_pts else None
+
+        def fwd():
+            mpt.enumerate_candidates(ds, max_order, spec, out=cands, stream=stream)
+            mpt.solve(ds, cands, precision, sch, out=sols, stream=stream)
+            mpt.validate(ds, cands, sols, out=paths, stream=stream)
+
+        def fwd_bwd():
+            fwd()
+            mpt.grad(ds, cands, paths, g_len, g_pts, stream=stream)
+
+        fwd()
+        stream.synchronize()
+        out = {"candidates": n, "valid_paths_per_step": paths.n()}
+        t = timed(stream, fwd, reps, flush)
+        out.update({"ms_per_step": t, "solves_per_sec": n / (t * 1e-3), "valid_paths_per_sec": paths.n() / (t * 1e-3)})
+        if grad_pts:
+            tb = timed(stream, fwd_bwd, reps, flush)
+            out.update({"forward_backward_ms": tb, "forward_only_ms": t})
+        if graph:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                fwd()
+            g.replay()
+            stream.synchronize()
+            out["cuda_graph_ms"] = timed(stream, g.replay, reps, flush)
+            del g
+        del cands, sols, paths, g_len, g_pts, ds
+        torch.cuda.empty_cache()
+        return out
+
+    # street canyon: the plain FP64 method of its config, and FP32 + refinement
+    sc = scenes.street_canyon()
+    legs["street_canyon_fp64_plain"] = trace_leg(sc, scenes.CONFIG_SPECS["street_canyon"], 2, mpt.FP64_PLAIN)
+    legs["street_canyon_fp32_refine"] = trace_leg(sc, scenes.CONFIG_SPECS["street_canyon"], 2)
+    # mixed orders 1-4: library defaults, then the autotuned schedule (eager and graph)
+    sc = scenes.mixed_order_city()
+    spec = scenes.CONFIG_SPECS["mixed_order"]
+    legs["mixed_orders_default"] = trace_leg(sc, spec, 4, graph=True)
+    ds = mpt.DeviceScene(ctx, sc)
+    cands = mpt.enumerate_candidates(ds, 4, spec, stream=stream)
+    best, best_ms = mpt.autotune(ds, cands, stream=stream)
+    del cands, ds
+    torch.cuda.empty_cache()
+    legs["mixed_orders_tuned"] = trace_leg(sc, spec, 4, sch=best, graph=True)
+    legs["mixed_orders_tuned"]["schedule"] = mpt.schedule_dict(best)
+    # curved geometry, 4,096 pairs, 8 starts for curved sequences
+    legs["curved_4096pairs"] = trace_leg(scenes.curved_scene(), scenes.CONFIG_SPECS["curved"], 3)
+    # differentiable block, 64x64 RX: forward alone and forward + adjoint
+    legs["differentiable_64x64rx"] = trace_leg(scenes.urban_block(64), scenes.CONFIG_SPECS["differentiable"], 2,
+                                               grad_pts=True)
+    # image method beside the minimiser on the urban block's reflection-only candidates
+    ub = scenes.urban_block(32)
+    keep = np.nonzero(ub.obj_kind == scenes.PLANE)[0]
+    planes = scenes.Scene("urban_block_planes", ub.scale, ub.obj_kind[keep], ub.obj_param[keep], ub.occ_kind,
+                          ub.occ_param, ub.tx, ub.rx, ub.pair_mode, ub.meta).contiguous()
+    spec2 = scenes.SequenceSpec(quota=(-1, -1, 0, 0))
+    ds = mpt.DeviceScene(ctx, planes)
+    cands = mpt.enumerate_candidates(ds, 2, spec2, stream=stream)
+    sols = mpt.alloc_solutions(cands.capacity, dev)
+    paths = mpt.alloc_paths(1 << 20, dev)
+    im = {"candidates": cands.capacity}
+    im["image_method_ms"] = timed(stream, lambda: mpt.image_method(ds, cands, out=sols, stream=stream), reps, flush)
+    mpt.validate(ds, cands, sols, out=paths, stream=stream)
+    stream.synchronize()
+    im["image_method_valid"] = paths.n()
+    im["minimiser_ms"] = timed(stream, lambda: mpt.solve(ds, cands, mpt.FP32_FP64REFINE, out=sols, stream=stream),
+                               reps, flush)
+    mpt.validate(ds, cands, sols, out=paths, stream=stream)
+    stream.synchronize()
+    im["minimiser_valid"] = paths.n()
+    im["minimiser_over_image_method"] = im["minimiser_ms"] / im["image_method_ms"]
+    legs["image_method_vs_minimiser_urban_block_planes"] = im
+    del cands, sols, paths, ds
+    torch.cuda.empty_cache()
+    return legs
+
+
 def run_ours(args):
     ws, rank, local = dist_env()
     import torch.distributed as dist
@@ -236,26 +359,31 @@ def run_ours(args):
         g_rx = torch.zeros_like(ds.rx)
         g_obj = torch.zeros(sc.n_obj, dtype=torch.float64, device=dev)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        # the schedule of the solve: mpt_autotune's choice for this workload
+        mpt.enumerate_candidates(ds, 2, spec, out=cands, stream=stream)
+        if args.no_tune:
+            sched = mpt.schedule_struct()
+        else:
+            sched, _ = mpt.autotune(ds, cands, out=sols, stream=stream)
 
         def step(precision=mpt.FP32_FP64REFINE, ev=None):
             mpt.enumerate_candidates(ds, 2, spec, out=cands, stream=stream)
             if ev is not None:
                 ev[0].record(stream)
-            mpt.solve(ds, cands, precision, out=sols, stream=stream)
+            mpt.solve(ds, cands, precision, sched, out=sols, stream=stream)
             if ev is not None:
                 ev[1].record(stream)
             mpt.validate(ds, cands, sols, out=paths, stream=stream)
             mpt.grad(ds, cands, paths, g_len, g_tx=g_tx, g_rx=g_rx, g_obj=g_obj, stream=stream)
-
         for _ in range(args.warmup):
             step()
         stream.synchronize()
         n_valid = paths.n()
         flops = algorithmic_flops(mpt, sc, cands, sols, n_cand)
-        # enumerate (2) + solve (endpoint copy, 4 orders x {solver, visibility
-        # prescreen, refinement, refinement fallback}) + validate (list, test, scan, scatter, fill) +
-        # adjoint (one launch per order)
-        launches_per_step = 2 + (1 + 4 * 4) + 5 + 4
+        # enumerate (2) + solve (endpoint copy, solver launches, per order the
+        # visibility prescreen if on, refinement and its fallback) + validate
+        # (list, test, scan, scatter, fill) + adjoint (one launch per order)
+        launches_per_step = 2 + solve_launches(mpt, sched) + 5 + 4
 
         # ---- device-resident timing
         ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -353,7 +481,7 @@ def run_ours(args):
             V = mpt.visibility(ds, stream=stream)
             b.record(stream)
             mpt.enumerate_candidates(ds, 2, spec, adj=V, out=pr_cands, stream=stream)
-            mpt.solve(ds, pr_cands, mpt.FP32_FP64REFINE, out=sols, stream=stream)
+            mpt.solve(ds, pr_cands, mpt.FP32_FP64REFINE, sched, out=sols, stream=stream)
             mpt.validate(ds, pr_cands, sols, out=paths, stream=stream)
             mpt.grad(ds, pr_cands, paths, g_len, g_tx=g_tx, g_rx=g_rx, g_obj=g_obj, stream=stream)
             c2.record(stream)
@@ -372,7 +500,7 @@ def run_ours(args):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            mpt.solve(ds, cands, mpt.FP32, out=sols, stream=stream)
+            mpt.solve(ds, cands, mpt.FP32, sched, out=sols, stream=stream)
             b.record(stream)
             stream.synchronize()
             mini_ms.append(a.elapsed_time(b))
@@ -398,7 +526,7 @@ def run_ours(args):
             t0 = time.perf_counter()
             ds_e = mpt.DeviceScene(ctx, sc, tx_host=tx_h, rx_host=rx_h)  # scene + endpoints host -> device
             mpt.enumerate_candidates(ds_e, 2, spec, out=cands, stream=stream)
-            mpt.solve(ds_e, cands, mpt.FP32_FP64REFINE, out=sols, stream=stream)
+            mpt.solve(ds_e, cands, mpt.FP32_FP64REFINE, sched, out=sols, stream=stream)
             mpt.validate(ds_e, cands, sols, out=paths, stream=stream)
             g_tx.zero_()
             mpt.grad(ds_e, cands, paths, g_len, g_tx=g_tx, g_rx=g_rx, g_obj=g_obj, stream=stream)
@@ -414,6 +542,11 @@ def run_ours(args):
             ds_e.free()
         e2e_ms_step = float(np.median(e2e_ms))
         e2e_ms_step = max_over_ranks(e2e_ms_step, dev)
+        legs = None
+        if not args.no_legs and rank == 0:
+            del pr_cands
+            torch.cuda.empty_cache()
+            legs = workload_legs(mpt, ctx, dev, stream, flush, max(3, min(args.steps, 10)))
 
     solve_avg_ms = float(np.mean(solve_ms))
     achieved = flops / (solve_avg_ms * 1e-3) / 1e12
@@ -430,11 +563,12 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32+f64",
+        "dtype": "f32+ff48 (fp64 storage)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD if args.rx_side == 32 else f"{WORKLOAD} (rx grid {args.rx_side}x{args.rx_side})",
                    "candidates_per_gpu": n_cand, "max_order": 2,
-                   "precision": "fp32 iterations; float-float refinement of prescreened candidates (fp64 results); fp64 acceptance decisions near the margins",
+                   "precision": "fp32 iterations; float-float refinement of prescreened candidates (fp64 results); fp64 fallback solve of ill-conditioned ones; fp64 acceptance decisions near the margins",
+                   "schedule": mpt.schedule_dict(sched) | {"source": "defaults" if args.no_tune else "mpt_autotune"},
                    "step": "enumerate + solve + validate/compact + adjoint",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write), outside the step events",
                    "parallelism": f"weak: one process per GPU, {ws} GPU(s)"},
@@ -458,7 +592,8 @@ def run_ours(args):
         "e2e": {"value": n_cand * ws / (e2e_ms_step * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms_step,
                 "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_bytes)},
         "gpu_launches": launches_per_step * args.steps,
-        "clocks": clk,
+        "clocks": clk | ({"sm_cycles_per_step": ms_per_step * 1e3 * clk["sm_mhz"]} if clk.get("sm_mhz") else {}),
+        "workloads": legs,
         "wall_s_timed_region": t_wall,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -552,11 +687,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-legs", action="store_true", help="skip the per-workload legs")
+    ap.add_argument("--no-tune", action="store_true", help="library default schedule instead of mpt_autotune")
     ap.add_argument("--ref-entries", type=int, default=64)
     ap.add_argument("--rx-side", type=int, default=32, help="RX grid side (32 = the benchmark workload)")
     ap.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)

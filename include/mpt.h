@@ -271,6 +271,48 @@ int mpt_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
               const mpt_candidates* cand, int precision, const mpt_schedule* schedule,
               mpt_solutions* out, void* stream);
 
+/* Image method (Sec. III-A, Eqs. 5-6), the paper's baseline, for the
+ * candidates whose objects are all planes (reflection-only sequences).  For
+ * each candidate of the ranges in cand->order_begin (the first
+ * min(*cand->count, cand->capacity) candidates), one launch per order: forward
+ * images of TX through the planes (Eq. 5), then the points back from RX
+ * (Eq. 6), X_k = X_{k+1} + lambda_k (X_{k+1} - I_k), in float-float
+ * arithmetic (48-bit significand), stored as FP64.  Output in `out`, the
+ * layout of mpt_solve:
+ *   - planar candidate whose path exists on the unbounded planes (every
+ *     lambda_k strictly in (-1, 0)): T = plane parameters of its points,
+ *     cost 0, status MPT_PATH_CONVERGED | MPT_PATH_REFINED;
+ *   - planar candidate without such a path: cost +inf, status
+ *     MPT_PATH_STALLED | MPT_PATH_REFINED (T holds the unchecked points);
+ *   - any other candidate (an edge or a curved object in its sequence):
+ *     cost +inf, status MPT_PATH_NONFINITE, T untouched.
+ * mpt_validate then applies bounds, minimum segment length and visibility, as
+ * for the minimiser's solutions.  iters and evals are written 0.  Errors:
+ * MPT_ERR_ARG on null arguments, MPT_ERR_CAPACITY when out->capacity <
+ * cand->capacity. */
+int mpt_image_method(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
+                     const mpt_candidates* cand, mpt_solutions* out, void* stream);
+
+/* Autotuner of mpt_solve's schedule for one workload (the batching of
+ * Algorithm 1's loop over candidates and starts; the paper has no
+ * counterpart).  Times mpt_solve on `cand` with `precision` under schedules
+ * that differ only in knobs that leave every valid path unchanged (tile,
+ * refill_min, blocks_per_sm, mixed_orders, prescreen; the iteration cap is
+ * part of the method and is not searched): a coordinate descent from the
+ * defaults, two sweeps, each schedule timed with CUDA events as the best of
+ * two solves.  *best receives the fastest schedule (pass it to mpt_solve),
+ * *best_ms (may be NULL) its time.  The choice is cached in the context by a
+ * workload signature (the scene's content hash, the candidate count and
+ * per-order ranges, the endpoints' shape, the precision and the starts'
+ * seed): a later call on the same workload returns it without timing.  The
+ * call synchronises `stream` (it reads the order ranges back and waits for
+ * its timings) and runs mpt_solve several times into `out`, which holds the
+ * last trial's solutions on return (any tried schedule yields the same valid
+ * paths).  Errors as mpt_solve. */
+int mpt_autotune(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
+                 const mpt_candidates* cand, int precision, mpt_solutions* out, mpt_schedule* best,
+                 double* best_ms, void* stream);
+
 /* ------------------------------------------------------------- validate */
 
 /* Acceptance of Algorithm 1: cost < tau (FP64), every segment longer than

@@ -133,6 +133,7 @@ int mpt_ctx_create(int device, mpt_ctx** out) {
   c->rscratch_bytes = 0;
   c->escratch = nullptr;
   c->escratch_bytes = 0;
+  c->tune_cache = nullptr;
   *out = c;
   return MPT_OK;
 }
@@ -150,6 +151,7 @@ int mpt_ctx_destroy(mpt_ctx* ctx) {
     cudaEventDestroy(ctx->ev_join[i]);
   }
   cudaEventDestroy(ctx->ev_fork);
+  mpt::tune_cache_free(ctx);
   delete ctx;
   return MPT_OK;
 }
@@ -222,6 +224,16 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   std::vector<float> a32((size_t)no * 16);
   for (int o = 0; o < no; ++o)
     for (int i = 0; i < 16; ++i) a32[(size_t)16 * o + i] = (float)ov[(size_t)16 * o + i];
+  // object-major float-float copy (head, tail) for the refinement, the
+  // adjoint and the image method: value = head + tail to about 48 bits
+  std::vector<float> aff((size_t)no * 32);
+  for (int o = 0; o < no; ++o)
+    for (int i = 0; i < 16; ++i) {
+      const double v = ov[(size_t)16 * o + i];
+      const float hi = (float)v;
+      aff[(size_t)32 * o + 2 * i] = hi;
+      aff[(size_t)32 * o + 2 * i + 1] = (float)(v - (double)hi);
+    }
   for (int o = 0; o < nc; ++o)
     for (int i = 0; i < 16; ++i) {
       c32[((size_t)(i / 4) * nc + o) * 4 + (i % 4)] = (float)cv[(size_t)16 * o + i];
@@ -323,7 +335,7 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
                s_o64 = align256((size_t)no * 128), s_ck = align256((size_t)nc * 4 + 4),
                s_c32 = align256((size_t)nc * 64 + 16), s_c64 = align256((size_t)nc * 128 + 16),
                s_oo = align256((size_t)no * 16), s_cb = align256((size_t)nc * 32 + 16),
-               s_a32 = align256((size_t)no * 64);
+               s_a32 = align256((size_t)no * 64), s_aff = align256((size_t)no * 128);
   // boxes of groups of OCC_GROUP consecutive occluders (union of the members'
   // boxes): a segment that misses a group's box skips its members
   const int ng = (nc + mpt::OCC_GROUP - 1) / mpt::OCC_GROUP;
@@ -341,7 +353,7 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
     }
   }
   const size_t s_gb = align256((size_t)ng * 32 + 16);
-  const size_t total = s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb + s_a32 + s_gb;
+  const size_t total = s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb + s_a32 + s_gb + s_aff;
   MPT_CUDA_TRY(cudaSetDevice(ctx->device));
   void* mem = nullptr;
   MPT_CUDA_TRY(cudaMalloc(&mem, total));
@@ -376,7 +388,9 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   d.a32 = reinterpret_cast<const float4*>(put(a32.data(), (size_t)no * 64, s_a32));
   d.n_grp = ng;
   d.gbox = reinterpret_cast<const float4*>(put(gbox.data(), (size_t)ng * 32, s_gb));
+  d.aff = reinterpret_cast<const float4*>(put(aff.data(), (size_t)no * 128, s_aff));
   d.scale = desc->scale;
+  s->signature = fnv1a(image.data(), total, fnv1a(&desc->scale, sizeof(double)));
   cudaError_t e = cudaMemcpy(mem, image.data(), total, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -431,6 +445,34 @@ int mpt_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, c
   if (cand->capacity > INT32_MAX) return MPT_ERR_CAPACITY;  // per-order offsets are 32-bit
   if (cand->capacity == 0) return MPT_OK;
   return launch_solve(ctx, scene, ends, cand, precision, schedule, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mpt_autotune(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
+                 int precision, mpt_solutions* out, mpt_schedule* best, double* best_ms, void* stream) {
+  if (!ctx || !scene || !cand || !out || !best || !cand->rec || !cand->order_begin || !out->T || !out->cost ||
+      !out->status || !out->iters || !out->evals)
+    return MPT_ERR_ARG;
+  if (check_ends(ends) != MPT_OK) return MPT_ERR_ARG;
+  if (precision != MPT_FP64_PLAIN && precision != MPT_FP32 && precision != MPT_FP32_FP64REFINE) return MPT_ERR_ARG;
+  if (out->capacity < cand->capacity) return MPT_ERR_CAPACITY;
+  if (cand->capacity > INT32_MAX) return MPT_ERR_CAPACITY;
+  if (cand->capacity == 0) {
+    *best = mpt_schedule{};
+    best->block = SOLVE_BLOCK;
+    if (best_ms) *best_ms = 0.0;
+    return MPT_OK;
+  }
+  return autotune(ctx, scene, ends, cand, precision, out, best, best_ms, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mpt_image_method(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
+                     mpt_solutions* out, void* stream) {
+  if (!ctx || !scene || !cand || !out || !cand->rec || !cand->count || !cand->order_begin || !out->T ||
+      !out->cost || !out->status || !out->iters || !out->evals)
+    return MPT_ERR_ARG;
+  if (check_ends(ends) != MPT_OK) return MPT_ERR_ARG;
+  if (out->capacity < cand->capacity) return MPT_ERR_CAPACITY;
+  return launch_image(ctx, scene, ends, cand, out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int mpt_validate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,

@@ -29,6 +29,7 @@ struct DevScene {
   const float4* cbox;       // [2][n_occ]: occluder boxes (lo, hi) grown by 1 cm; lo.w = 0 rectangle, 1 paraboloid
   int n_grp;                // ceil(n_occ / OCC_GROUP)
   const float4* gbox;       // [2][n_grp]: boxes of groups of OCC_GROUP consecutive occluders
+  const float4* aff;        // [n_obj][8]: float-float records (head, tail) x 16, object-major
   double scale;
 };
 
@@ -110,14 +111,16 @@ __device__ __forceinline__ Rec<double> load_obj64(const DevScene& s, int o) {
   return r;
 }
 
-// Scene values in float-float (the refinement's working precision).
+// Scene values in float-float (the refinement's working precision), from
+// the copy split into head and tail at upload.
 __device__ __forceinline__ Rec<ff> load_obj_ff(const DevScene& s, int o) {
   Rec<ff> r;
+  const float4* p = s.aff + 8 * o;
 #pragma unroll
   for (int f = 0; f < 8; ++f) {
-    const double2 q = __ldg(&s.o64[f * s.n_obj + o]);
-    r.v[2 * f] = ff_from_double(q.x);
-    r.v[2 * f + 1] = ff_from_double(q.y);
+    const float4 q = __ldg(p + f);
+    r.v[2 * f] = ff(q.x, q.y);
+    r.v[2 * f + 1] = ff(q.z, q.w);
   }
   return r;
 }
@@ -187,6 +190,8 @@ struct mpt_ctx {
   // fork them from and join them back to the caller's stream
   cudaStream_t aux[3];
   cudaEvent_t ev_fork, ev_join[3];
+  // schedules chosen by mpt_autotune, by workload signature (tune.cu)
+  void* tune_cache;
 };
 
 // Makes the auxiliary streams wait for the work enqueued on st so far.
@@ -211,6 +216,7 @@ struct mpt_scene {
   void* alloc;             // one device allocation holding every array
   int32_t* host_kind;      // host copy of the kinds
   int n_obj;
+  uint64_t signature;      // FNV-1a hash of the uploaded image (workload key of mpt_autotune)
 };
 
 #define MPT_CUDA_TRY(expr)                                                 \
@@ -260,6 +266,17 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
 int launch_enumerate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, int max_order,
                      const uint8_t* adj, const mpt_sampling* smp, mpt_candidates* out, cudaStream_t st);
 int launch_visibility(mpt_ctx* ctx, const mpt_scene* scene, uint8_t* vis, cudaStream_t st);
+int launch_image(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
+                 mpt_solutions* out, cudaStream_t st);
+void tune_cache_free(mpt_ctx* ctx);
+int autotune(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
+             int precision, mpt_solutions* out, mpt_schedule* best, double* best_ms, cudaStream_t st);
+// FNV-1a (Fowler, Noll, Vo) over a byte range, continuing from h.
+inline uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
 int launch_field(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
                  const mpt_paths* paths, const int64_t* d_valid_count, const mpt_field_params* fp, double* field,
                  cudaStream_t st);

@@ -647,8 +647,8 @@ __global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? (PREC == MPT_FP64_PLAIN
 // persistent grid): warps claim CHUNK-sized pieces of the whole candidate
 // range and solve each piece with the solver of its order (a piece that
 // straddles an order boundary is split).  Registers are those of the order-4
-// solver, so per-order launches are faster when the orders are known to
-// come in large uniform ranges; the autotuner chooses.
+// solver, so per-order launches are faster when the orders come in large
+// uniform ranges; mpt_autotune times both for a workload.
 template <int PREC>
 __global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_mixed(DevScene sc, DevEnds ep, const float4* ends32,
                                                           CandView cv, SolView out, SolveCfg cfg,

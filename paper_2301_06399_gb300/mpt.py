@@ -68,7 +68,7 @@ _lock = threading.Lock()
 SYMBOLS = ["mpt_ctx_create", "mpt_ctx_destroy", "mpt_ctx_sm_count", "mpt_ctx_check", "mpt_scene_upload",
            "mpt_scene_free", "mpt_enumerate", "mpt_candidate_count", "mpt_solve", "mpt_validate", "mpt_grad",
            "mpt_status_string", "mpt_flop_model", "mpt_validate_noalloc", "mpt_visibility", "mpt_field",
-           "mpt_ctx_selftest_wait"]
+           "mpt_ctx_selftest_wait", "mpt_image_method", "mpt_autotune"]
 
 
 def library_path() -> str:
@@ -100,6 +100,10 @@ def lib():
             L.mpt_candidate_count.argtypes = [P, C.POINTER(Endpoints), C.c_int, C.POINTER(Sampling)]
             L.mpt_solve.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct), C.c_int,
                                     C.POINTER(Schedule), C.POINTER(SolStruct), P]
+            L.mpt_autotune.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct), C.c_int,
+                                       C.POINTER(SolStruct), C.POINTER(Schedule), C.POINTER(D), P]
+            L.mpt_image_method.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct), C.POINTER(SolStruct),
+                                           P]
             L.mpt_validate.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct), C.POINTER(SolStruct),
                                        D, C.POINTER(PathStruct), P, P]
             L.mpt_validate_noalloc.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct),
@@ -315,6 +319,40 @@ def solve(ds: DeviceScene, cands: Candidates, precision: int = FP32_FP64REFINE, 
     _check(lib().mpt_solve(ds.ctx.h, ds.h, C.byref(ep), C.byref(cs), precision,
                            C.byref(schedule) if schedule is not None else None, C.byref(ss), _stream(stream)),
            "mpt_solve")
+    return out
+
+
+def autotune(ds: DeviceScene, cands: Candidates, precision: int = FP32_FP64REFINE, out: Solutions | None = None,
+             stream=None) -> tuple[Schedule, float]:
+    """mpt_autotune: the fastest schedule of mpt_solve for this workload and
+    its time (ms); cached in the context by workload signature."""
+    if out is None:
+        out = alloc_solutions(cands.capacity, ds.tx.device)
+    ep = ds.endpoints()
+    cs = cands.struct()
+    ss = out.struct()
+    best = Schedule()
+    ms = D()
+    _check(lib().mpt_autotune(ds.ctx.h, ds.h, C.byref(ep), C.byref(cs), precision, C.byref(ss), C.byref(best),
+                              C.byref(ms), _stream(stream)), "mpt_autotune")
+    return best, ms.value
+
+
+def schedule_dict(s: Schedule) -> dict:
+    return {name: getattr(s, name) for name, _ in Schedule._fields_}
+
+
+def image_method(ds: DeviceScene, cands: Candidates, out: Solutions | None = None, stream=None) -> Solutions:
+    """Image method (Sec. III-A, Eqs. 5-6) for the reflection-only planar
+    candidates, in the layout of solve(); validate() applies bounds and
+    visibility."""
+    if out is None:
+        out = alloc_solutions(cands.capacity, ds.tx.device)
+    ep = ds.endpoints()
+    cs = cands.struct()
+    ss = out.struct()
+    _check(lib().mpt_image_method(ds.ctx.h, ds.h, C.byref(ep), C.byref(cs), C.byref(ss), _stream(stream)),
+           "mpt_image_method")
     return out
 
 

@@ -126,3 +126,58 @@ def test_differentiable_block_every_candidate_and_adjoint(mpt, ctx):
         print(f"adjoint over {n} paths ({'length and point' if with_pts else 'length'} weights): relative error "
               f"TX {e_tx:.1e}, RX {e_rx:.1e}, plane offsets {e_obj:.1e}")
         assert e_tx < 1e-6 and e_rx < 1e-6 and e_obj < 1e-6
+
+
+def _planes_only(sc):
+    """The scene's planes alone (edges dropped, occluders kept): every
+    candidate sequence is reflection-only."""
+    keep = np.nonzero(sc.obj_kind == S.PLANE)[0]
+    return S.Scene(sc.name + "_planes", sc.scale, sc.obj_kind[keep], sc.obj_param[keep], sc.occ_kind, sc.occ_param,
+                   sc.tx, sc.rx, sc.pair_mode, sc.meta).contiguous()
+
+
+@pytest.mark.parametrize("name", ["street_canyon", "urban_block_planes"])
+def test_image_method_matches_oracle_and_minimiser(mpt, ctx, name):
+    """The image method on the GPU (Sec. III-A, Eqs. 5-6) over every
+    reflection-only candidate: its valid set (after mpt_validate's bounds and
+    visibility) equals the FP64 oracle's and the minimiser's, points within
+    1e-6 m of the oracle's."""
+    sc = S.street_canyon() if name == "street_canyon" else _planes_only(S.urban_block(32))
+    spec = S.SequenceSpec(quota=(-1, -1, 0, 0))
+    ds = mpt.DeviceScene(ctx, sc)
+    cands = mpt.enumerate_candidates(ds, 2, spec)
+    im = mpt.image_method(ds, cands)
+    p_im = mpt.validate(ds, cands, im, capacity=1 << 21)
+    sols = mpt.solve(ds, cands, mpt.FP32_FP64REFINE)
+    p_mpt = mpt.validate(ds, cands, sols, capacity=1 << 21)
+    torch.cuda.synchronize()
+    table = oracle.enumerate_sequences(sc, 2, spec)
+    rep = F.compare_workload(sc, table, F.gpu_side(p_im), keep_sets=True)
+    a = p_im.cand[:p_im.n()].cpu().numpy()
+    b = p_mpt.cand[:p_mpt.n()].cpu().numpy()
+    print(f"\nPER-CONFIG image_method_{name}: {rep.summary()}; minimiser valid {len(b)}, equal sets {np.array_equal(a, b)}")
+    assert rep.ok(), rep.summary()
+    assert np.array_equal(a, b)
+    assert (p_im.X[:, :len(a)] - p_mpt.X[:, :len(b)]).abs().max().item() < 1e-6
+
+
+def test_autotuned_schedule_keeps_the_oracle_valid_set(mpt, ctx):
+    """mpt_autotune on the mixed-order city (orders 1-4, 2,097,152
+    candidates): the schedule it picks gives exactly the oracle's valid set,
+    and a second call on the same workload returns the cached choice."""
+    import time
+
+    sc = S.mixed_order_city()
+    spec = S.CONFIG_SPECS["mixed_order"]
+    ds = mpt.DeviceScene(ctx, sc)
+    cands = mpt.enumerate_candidates(ds, 4, spec)
+    t0 = time.perf_counter()
+    best, ms = mpt.autotune(ds, cands)
+    t1 = time.perf_counter()
+    again, ms2 = mpt.autotune(ds, cands)
+    t2 = time.perf_counter()
+    print(f"\nautotune mixed orders: {mpt.schedule_dict(best)}, {ms:.3f} ms per solve; search {t1 - t0:.2f} s, "
+          f"cached call {1e3 * (t2 - t1):.2f} ms")
+    assert mpt.schedule_dict(again) == mpt.schedule_dict(best) and ms2 == ms
+    assert t2 - t1 < 0.05 < t1 - t0
+    _check_full_set(mpt, ctx, sc, spec, 4, "mixed_orders_autotuned", best)
