@@ -225,6 +225,21 @@ int mpt_ctx_sm_count(const mpt_ctx* ctx);
 int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out);
 int mpt_scene_free(mpt_scene* scene);
 
+/* Plane offsets moved on the device, for gradients with respect to them
+ * (the differentiable configuration varies each wall's offset d in
+ * <n, X> = d; not in the paper).  dst must come from mpt_scene_upload of a
+ * description of the same sizes and kinds as base (typically the same one).
+ * Enqueued on `stream`: dst receives base's device image, then every plane
+ * object i with delta[i] != 0 (delta: device double [n_obj]; other kinds'
+ * entries ignored) moves along its normal by delta[i]: its corner and offset
+ * in every copy of its record, and the occluder rectangle that is its own
+ * facet, with that rectangle's bounding box; the boxes of the occluder groups
+ * are rebuilt.  Edges, other occluders and validation's lists of rectangles
+ * that hold an object's points stay base's.  No host round trip.  Errors:
+ * MPT_ERR_ARG on null arguments, base == dst or mismatched scenes. */
+int mpt_scene_shift_planes(mpt_ctx* ctx, const mpt_scene* base, mpt_scene* dst, const double* delta,
+                           void* stream);
+
 /* ---------------------------------------------------------- candidates */
 
 /* Visibility matrix V of Algorithm 1 (its first line; Sec. III, Fig. 5),

@@ -247,6 +247,7 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   // cross it strictly (the visibility rule needs both ends more than 1e-6 m
   // off the plane), so validation skips them; up to 4 per object.
   std::vector<int32_t> obj_occ((size_t)no * 4, -1);
+  std::vector<int32_t> own_occ((size_t)no, -1);  // the occluder that is a plane's own facet
   auto plane_dist = [&](const double* q, const double* X) {
     return (X[0] - q[0]) * q[12] + (X[1] - q[1]) * q[13] + (X[2] - q[2]) * q[14];
   };
@@ -265,7 +266,11 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
         // same corner, axes and extents (values 0..10 of both records)
         bool same = true;
         for (int i = 0; i < 11; ++i) same = same && a[i] == b[i];
-        if (same) { add_own(q); break; }
+        if (same) {
+          add_own(q);
+          own_occ[(size_t)o] = q;
+          break;
+        }
       }
     }
     for (int q = 0; q < nc; ++q) {
@@ -335,7 +340,8 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
                s_o64 = align256((size_t)no * 128), s_ck = align256((size_t)nc * 4 + 4),
                s_c32 = align256((size_t)nc * 64 + 16), s_c64 = align256((size_t)nc * 128 + 16),
                s_oo = align256((size_t)no * 16), s_cb = align256((size_t)nc * 32 + 16),
-               s_a32 = align256((size_t)no * 64), s_aff = align256((size_t)no * 128);
+               s_a32 = align256((size_t)no * 64), s_aff = align256((size_t)no * 128),
+               s_own = align256((size_t)no * 4);
   // boxes of groups of OCC_GROUP consecutive occluders (union of the members'
   // boxes): a segment that misses a group's box skips its members
   const int ng = (nc + mpt::OCC_GROUP - 1) / mpt::OCC_GROUP;
@@ -353,7 +359,7 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
     }
   }
   const size_t s_gb = align256((size_t)ng * 32 + 16);
-  const size_t total = s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb + s_a32 + s_gb + s_aff;
+  const size_t total = s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb + s_a32 + s_gb + s_aff + s_own;
   MPT_CUDA_TRY(cudaSetDevice(ctx->device));
   void* mem = nullptr;
   MPT_CUDA_TRY(cudaMalloc(&mem, total));
@@ -389,8 +395,10 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   d.n_grp = ng;
   d.gbox = reinterpret_cast<const float4*>(put(gbox.data(), (size_t)ng * 32, s_gb));
   d.aff = reinterpret_cast<const float4*>(put(aff.data(), (size_t)no * 128, s_aff));
+  d.own_occ = reinterpret_cast<const int32_t*>(put(own_occ.data(), (size_t)no * 4, s_own));
   d.scale = desc->scale;
   s->signature = fnv1a(image.data(), total, fnv1a(&desc->scale, sizeof(double)));
+  s->alloc_bytes = total;
   cudaError_t e = cudaMemcpy(mem, image.data(), total, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -445,6 +453,14 @@ int mpt_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, c
   if (cand->capacity > INT32_MAX) return MPT_ERR_CAPACITY;  // per-order offsets are 32-bit
   if (cand->capacity == 0) return MPT_OK;
   return launch_solve(ctx, scene, ends, cand, precision, schedule, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mpt_scene_shift_planes(mpt_ctx* ctx, const mpt_scene* base, mpt_scene* dst, const double* delta, void* stream) {
+  if (!ctx || !base || !dst || !delta || base == dst) return MPT_ERR_ARG;
+  if (base->alloc_bytes != dst->alloc_bytes || base->n_obj != dst->n_obj || base->d.n_occ != dst->d.n_occ ||
+      std::memcmp(base->host_kind, dst->host_kind, sizeof(int32_t) * (size_t)base->n_obj) != 0)
+    return MPT_ERR_ARG;
+  return launch_shift_planes(ctx, base, dst, delta, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int mpt_autotune(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,

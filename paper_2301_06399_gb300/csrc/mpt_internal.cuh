@@ -30,6 +30,7 @@ struct DevScene {
   int n_grp;                // ceil(n_occ / OCC_GROUP)
   const float4* gbox;       // [2][n_grp]: boxes of groups of OCC_GROUP consecutive occluders
   const float4* aff;        // [n_obj][8]: float-float records (head, tail) x 16, object-major
+  const int32_t* own_occ;   // [n_obj]: the occluder rectangle that is a plane's own facet, or -1
   double scale;
 };
 
@@ -217,6 +218,7 @@ struct mpt_scene {
   int32_t* host_kind;      // host copy of the kinds
   int n_obj;
   uint64_t signature;      // FNV-1a hash of the uploaded image (workload key of mpt_autotune)
+  size_t alloc_bytes;      // size of `alloc`
 };
 
 #define MPT_CUDA_TRY(expr)                                                 \
@@ -269,6 +271,7 @@ int launch_visibility(mpt_ctx* ctx, const mpt_scene* scene, uint8_t* vis, cudaSt
 int launch_image(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
                  mpt_solutions* out, cudaStream_t st);
 void tune_cache_free(mpt_ctx* ctx);
+int launch_shift_planes(mpt_ctx* ctx, const mpt_scene* base, mpt_scene* dst, const double* delta, cudaStream_t st);
 int autotune(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
              int precision, mpt_solutions* out, mpt_schedule* best, double* best_ms, cudaStream_t st);
 // FNV-1a (Fowler, Noll, Vo) over a byte range, continuing from h.

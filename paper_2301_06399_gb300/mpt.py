@@ -68,7 +68,7 @@ _lock = threading.Lock()
 SYMBOLS = ["mpt_ctx_create", "mpt_ctx_destroy", "mpt_ctx_sm_count", "mpt_ctx_check", "mpt_scene_upload",
            "mpt_scene_free", "mpt_enumerate", "mpt_candidate_count", "mpt_solve", "mpt_validate", "mpt_grad",
            "mpt_status_string", "mpt_flop_model", "mpt_validate_noalloc", "mpt_visibility", "mpt_field",
-           "mpt_ctx_selftest_wait", "mpt_image_method", "mpt_autotune"]
+           "mpt_ctx_selftest_wait", "mpt_image_method", "mpt_autotune", "mpt_scene_shift_planes"]
 
 
 def library_path() -> str:
@@ -100,6 +100,7 @@ def lib():
             L.mpt_candidate_count.argtypes = [P, C.POINTER(Endpoints), C.c_int, C.POINTER(Sampling)]
             L.mpt_solve.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct), C.c_int,
                                     C.POINTER(Schedule), C.POINTER(SolStruct), P]
+            L.mpt_scene_shift_planes.argtypes = [P, P, P, P, P]
             L.mpt_autotune.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct), C.c_int,
                                        C.POINTER(SolStruct), C.POINTER(Schedule), C.POINTER(D), P]
             L.mpt_image_method.argtypes = [P, P, C.POINTER(Endpoints), C.POINTER(CandStruct), C.POINTER(SolStruct),
@@ -215,6 +216,37 @@ class DeviceScene:
             self.free()
         except Exception:
             pass
+
+
+class SceneView:
+    """A scene already on the device with caller-provided device endpoints
+    (float64 [n, 3] tensors, used in place): what the calls need of a
+    DeviceScene, without copies."""
+
+    def __init__(self, ctx: Context, scene, handle, tx: torch.Tensor, rx: torch.Tensor):
+        self.ctx = ctx
+        self.scene = scene
+        self.h = handle
+        self.tx = tx
+        self.rx = rx
+        self.pair_mode = scene.pair_mode
+
+    def endpoints(self) -> Endpoints:
+        return Endpoints(self.tx.data_ptr(), self.tx.shape[0], self.rx.data_ptr(), self.rx.shape[0], self.pair_mode)
+
+    @property
+    def n_pairs(self) -> int:
+        return self.tx.shape[0] * self.rx.shape[0] if self.pair_mode == 0 else self.tx.shape[0]
+
+
+def shift_planes(base: DeviceScene, dst: DeviceScene, delta: torch.Tensor, stream=None) -> None:
+    """mpt_scene_shift_planes: dst <- base with plane i moved by delta[i]
+    (device float64 [n_obj]) along its normal."""
+    d = delta.detach().to(device=base.tx.device, dtype=torch.float64).contiguous()
+    if stream is not None and d.data_ptr() != delta.data_ptr():
+        d.record_stream(stream)  # a converted copy lives until the launch has read it
+    _check(lib().mpt_scene_shift_planes(base.ctx.h, base.h, dst.h, C.c_void_p(d.data_ptr()), _stream(stream)),
+           "mpt_scene_shift_planes")
 
 
 def sampling_struct(spec) -> Sampling:

@@ -610,3 +610,52 @@ def test_bounded_wait_reports_timeout_and_the_context_stays_usable(mpt, ctx):
     table = oracle.enumerate_sequences(sc, 2, spec)
     n_valid, _, _, _ = compare_entries(sc, table, paths, range(len(table)), sc.n_pairs)
     assert n_valid == paths.n() > 0
+
+
+def _host_shifted(scene, delta):
+    """The scene with plane i moved by delta[i] along its normal, built on the
+    host (corner and offset of the plane, corner of its own rectangle)."""
+    s = S.Scene(scene.name, scene.scale, scene.obj_kind.copy(), scene.obj_param.copy(), scene.occ_kind.copy(),
+                scene.occ_param.copy(), scene.tx.copy(), scene.rx.copy(), scene.pair_mode, dict(scene.meta))
+    L, OL = S.OBJ_LAYOUT[S.PLANE], S.OCC_LAYOUT[S.OCC_RECT]
+    for i in np.nonzero(delta)[0]:
+        if s.obj_kind[i] != S.PLANE:
+            continue
+        p = s.obj_param[i]
+        n, O0 = p[L["n"]:L["n"] + 3].copy(), p[L["O"]:L["O"] + 3].copy()
+        for q in range(s.n_occ):
+            if s.occ_kind[q] == S.OCC_RECT and np.array_equal(s.occ_param[q, OL["O"]:OL["O"] + 3], O0) and \
+                    np.array_equal(s.occ_param[q, OL["u"]:OL["u"] + 3], p[L["u"]:L["u"] + 3]):
+                s.occ_param[q, OL["O"]:OL["O"] + 3] = O0 + delta[i] * n
+        p[L["d"]] += delta[i]
+        p[L["O"]:L["O"] + 3] = O0 + delta[i] * n
+    return s.contiguous()
+
+
+@pytest.mark.parametrize("which", ["ground_and_walls", "ground"])
+def test_device_plane_shift_equals_host_shift(mpt, ctx, which):
+    """mpt_scene_shift_planes (device) against a host-shifted re-upload: the
+    solver's output is bit-identical (same rounding of the shifted records);
+    with only the ground moved (no edge lies in its plane, so validation's
+    lists of rectangles holding an object agree) the valid paths are too."""
+    sc = S.urban_block(4)
+    spec = S.CONFIG_SPECS["urban_block"]
+    delta = np.zeros(sc.n_obj)
+    ground = int(np.nonzero(sc.obj_kind == S.PLANE)[0][-1])
+    delta[ground] = 0.3
+    if which == "ground_and_walls":
+        delta[[0, 5, 13, 22]] = [0.25, -0.4, 1.0, 0.05]
+    base = mpt.DeviceScene(ctx, sc)
+    dst = mpt.DeviceScene(ctx, sc)
+    mpt.shift_planes(base, dst, torch.as_tensor(delta).cuda())
+    view = mpt.SceneView(ctx, sc, dst.h, base.tx, base.rx)
+    r1 = mpt.trace(view, 2, spec, path_capacity=1 << 16)
+    r2 = mpt.trace(mpt.DeviceScene(ctx, _host_shifted(sc, delta)), 2, spec, path_capacity=1 << 16)
+    torch.cuda.synchronize()
+    n = int(r1.cands.count.item())
+    assert torch.equal(r1.sols.T[:, :n], r2.sols.T[:, :n]) and torch.equal(r1.sols.cost[:n], r2.sols.cost[:n])
+    assert torch.equal(r1.sols.status[:n], r2.sols.status[:n])
+    if which == "ground":
+        m = r1.paths.n()
+        assert m == r2.paths.n() > 100
+        assert torch.equal(r1.paths.cand[:m], r2.paths.cand[:m]) and torch.equal(r1.paths.X[:, :m], r2.paths.X[:, :m])
