@@ -629,10 +629,21 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
   __syncwarp();
 }
 
-// Orders 1-2 (the bulk of the work) of the FP32 solver are held to 102
-// registers: 5 blocks of 128 threads per SM.
+// Resident blocks per SM the register allocation is held to: orders 1-2 of
+// the FP32 solvers (the bulk of the work) 5 blocks of 128 threads (96
+// registers), 4 for scenes with curved objects (5 spilled: measured 3.5%
+// faster on the curved scene); orders 3-4 three (168 registers, no spill;
+// measured 5% faster on order 4 than two), curved order 4 two (three would
+// spill); the FP64 method fewer.
 template <int N, int PREC, bool CURVED>
-__global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? (PREC == MPT_FP64_PLAIN ? 2 : 5) : 1))
+constexpr int gn_min_blocks() {
+  if (PREC == MPT_FP64_PLAIN) return N <= 2 ? 2 : 1;
+  if (N <= 2) return CURVED ? 4 : 5;
+  return (N == 4 && CURVED) ? 2 : 3;
+}
+
+template <int N, int PREC, bool CURVED>
+__global__ void __launch_bounds__(SOLVE_BLOCK, gn_min_blocks<N, PREC, CURVED>())
     k_gn(DevScene sc, DevEnds ep, const float4* ends32, CandView cv, SolView out, SolveCfg cfg,
          unsigned long long* counter, RefineList rl) {
   __shared__ __align__(16) uint4 rbuf[GN_WARPS][2][GN_CHUNK];
