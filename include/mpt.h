@@ -194,7 +194,9 @@ typedef struct {
                              0 library default (on), 1 on, 2 off */
   int32_t fallback;       /* arithmetic of the refinement's fallback solve (the few
                              ill-conditioned candidates the mixed steps leave):
-                             0 library default (FP64), 1 float-float, 2 FP64 */
+                             0 library default (2), 1 float-float on one lane,
+                             2 FP64 with each candidate's evaluation spread over
+                             the lanes of a warp, 3 FP64 on one lane */
 } mpt_schedule;
 
 /* Compacted valid paths (caller-owned device buffers). */

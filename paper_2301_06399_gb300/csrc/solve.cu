@@ -42,7 +42,7 @@ struct SolveCfg {
   float mu32;
   double mu64;
   int prescreen;     // 1: visibility prescreen before the refinement
-  int fallback_f64;  // 1: refinement fallback in FP64, 0: float-float
+  int fallback;  // k_refine_fb mode: FB_FF, FB_F64 or FB_F64_WARP
 };
 
 struct CandView {
@@ -956,6 +956,226 @@ __device__ double gn_f64(const int (&kind)[N], const Rec<double> (&rec)[N], doub
   return cost;
 }
 
+// ------------------------------------------- FP64 fallback across a warp --
+// The FP64 pipe issues about one warp instruction per 80 cycles on each SM
+// sub-partition whatever the number of active lanes, so a lone candidate's
+// FP64 solve takes its count of FP64 warp instructions times that interval.
+// eval_lanes computes what eval_path<N, double, double, true> computes (the
+// cost of Eq. 15, J^T J and J^T rho) with the work split over the lanes of
+// one warp instead of repeated in each; lane L has the roles
+//   m = L / 2 < N:       point m (Eq. 13/14) and its tangent L % 2: Jacobian
+//                        column L (the parameter slot of that tangent) and
+//                        row L of J^T J
+//   L = 2m + 1, m <= N:  segment m (X_{m-1} -> X_m; X_{-1} = TX, X_N = RX):
+//                        unit vector and inverse length
+//   L = 2k, k < N:       interaction k: residual (Eq. 8 / ||i||, or Eq. 9)
+// and shuffles carry each piece to the lanes that use it.  Every value that
+// steers the iteration (cost, J^T J, J^T rho) is gathered in the same order
+// in every lane, so all lanes hold identical copies and take the same
+// branches.  Lanes with no role compute values nobody reads.
+// Every shuffle below runs in all 32 lanes (none sits in a branch); source
+// lanes outside the warp are clamped and their values discarded.
+__device__ __forceinline__ v3<double> shfl3(const v3<double>& v, int src) {
+  src = src < 0 ? 0 : (src > 31 ? 31 : src);
+  return mk(__shfl_sync(FULL, v.x, src), __shfl_sync(FULL, v.y, src), __shfl_sync(FULL, v.z, src));
+}
+__device__ __forceinline__ double shfl1(double v, int src) {
+  src = src < 0 ? 0 : (src > 31 ? 31 : src);
+  return __shfl_sync(FULL, v, src);
+}
+
+template <int N>
+__device__ double eval_lanes(const int (&kind)[N], const Rec<double>& rm, const double (&prm)[2 * N],
+                             const v3<double>& A, const v3<double>& B, double* jtj, double* g, bool& ok,
+                             int lane) {
+  constexpr int Q = 2 * N;
+  const int m = lane >> 1, j = lane & 1;
+  // this lane's point: object m, parameters (s, t) = prm[2m], prm[2m + 1]
+  int km = K_PLANE;
+  double s = 0.0, t = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if (k == m) {
+      km = kind[k];
+      s = prm[2 * k];
+      t = prm[2 * k + 1];
+    }
+  const PointT<double> pt = point_at<double, true, true>(km, rm, s, t);
+  // segment m: unit vector u and inverse length il (lanes 2m + 1)
+  const v3<double> Xprev = shfl3(pt.X, 2 * m - 2);
+  const v3<double> Xa = m == 0 ? A : Xprev;
+  const v3<double> Xb = m == N ? B : pt.X;
+  const v3<double> d = Xb - Xa;
+  const double l2 = dot(d, d);
+  const double il = rsq(l2);
+  const v3<double> u = d * il;
+  const bool seg_lane = (j == 1) && (m <= N);
+  ok = __ballot_sync(FULL, seg_lane && !(l2 > 0.0)) == 0u;
+  // interaction m (lanes 2m): ih = u_m, rh = u_{m+1}
+  const v3<double> ih = shfl3(u, 2 * m + 1), rh = shfl3(u, 2 * m + 3);
+  v3<double> ax = mk(0.0, 0.0, 0.0), de = ax, rho = ax;  // axis: normal or edge direction
+  double c = 0.0, inv_nn = 0.0;
+  if (!is_edge(km)) {
+    if (km == K_PLANE) {
+      ax = rm.f3(12);
+    } else {
+      const double q2 = rm.v[14];
+      const v3<double> nraw = axpy(-t * q2, rm.f3(4), axpy(-s * q2, rm.f3(0), rm.f3(8)));
+      inv_nn = rsq(dot(nraw, nraw));
+      ax = nraw * inv_nn;
+    }
+    c = dot(ih, ax);
+    rho = axpy(2.0 * c, ax, rh - ih);
+  } else {
+    if (km == K_LINE) {
+      ax = rm.f3(4);
+    } else {
+      double sn, cs;
+      sincos_(s, sn, cs);
+      ax = axpy(cs, rm.f3(8), rm.f3(4) * (-sn));
+      de = axpy(-sn, rm.f3(8), rm.f3(4) * (-cs));
+    }
+    rho.x = dot(ih, ax) - dot(rh, ax);
+  }
+  const double part = fma(rho.x, rho.x, fma(rho.y, rho.y, rho.z * rho.z));
+  double cost = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) cost += __shfl_sync(FULL, part, 2 * k);
+  // Jacobian column of this lane's slot (point m, tangent j); an edge's
+  // second slot is unused (zero column, pinned by the caller)
+  const bool live = (m < N) && !(j == 1 && is_edge(km));
+  const v3<double> w = j == 0 ? pt.w0 : pt.w1;
+  const v3<double> ui = ih, uo = rh;
+  const double li = shfl1(il, 2 * m + 1), lo = shfl1(il, 2 * m + 3);
+  const v3<double> PiW = axpy(-dot(ui, w), ui, w) * li;
+  const v3<double> PrW = axpy(-dot(uo, w), uo, w) * lo;
+  // own interaction m: the lane 2m values (this lane's own when j == 0)
+  const v3<double> ax_o = shfl3(ax, 2 * m), de_o = shfl3(de, 2 * m), rho_o = shfl3(rho, 2 * m);
+  const double c_o = shfl1(c, 2 * m), inn_o = shfl1(inv_nn, 2 * m);
+  // neighbours m - 1 and m + 1
+  const v3<double> ax_p = shfl3(ax, 2 * m - 2), rho_p = shfl3(rho, 2 * m - 2);
+  const v3<double> ax_n = shfl3(ax, 2 * m + 2), rho_n = shfl3(rho, 2 * m + 2);
+  int kp = K_PLANE, kn = K_PLANE;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    if (k + 1 == m) kp = kind[k];
+    if (k == m + 1) kn = kind[k];
+  }
+  const v3<double> zero = mk(0.0, 0.0, 0.0);
+  v3<double> cp = zero, co = zero, cn = zero;  // column blocks on interactions m-1, m, m+1
+  if (live) {
+    // interaction m - 1 sees this point as its next one: d rho / dX = Pi_m w
+    if (m >= 1) cp = is_edge(kp) ? mk(-dot(ax_p, PiW), 0.0, 0.0) : PiW;
+    // interaction m + 1 sees it as its previous one: H_{m+1}(Pr_m w)
+    if (m + 1 < N) cn = is_edge(kn) ? mk(-dot(ax_n, PrW), 0.0, 0.0) : axpy(-2.0 * dot(ax_n, PrW), ax_n, PrW);
+    if (!is_edge(km)) {
+      co = -(PrW + axpy(-2.0 * dot(ax_o, PiW), ax_o, PiW));
+      if (km == K_PARAB) {
+        const double q2 = rm.v[14];
+        const v3<double> craw = (j == 0 ? rm.f3(0) : rm.f3(4)) * (-q2);
+        const v3<double> dn = axpy(-dot(ax_o, craw), ax_o, craw) * inn_o;
+        co = axpy(2.0 * dot(ih, dn), ax_o, co);
+        co = axpy(2.0 * c_o, dn, co);
+      }
+    } else {
+      double v = dot(ax_o, PiW) + dot(ax_o, PrW);
+      if (km == K_ARC) v = v + dot(ih - rh, de_o);
+      co = mk(v, 0.0, 0.0);
+    }
+  }
+  double gp = dot(co, rho_o);
+  if (m >= 1) gp += dot(cp, rho_p);
+  if (m + 1 < N) gp += dot(cn, rho_n);
+  // the column over every interaction (zero away from m-1 .. m+1)
+  v3<double> col[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) col[k] = (k + 1 == m) ? cp : (k == m) ? co : (k == m + 1) ? cn : zero;
+  // row of J^T J: <col_L, col_q> over the interactions where column q lives
+  double row[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      if (k < (q >> 1) - 1 || k > (q >> 1) + 1) continue;
+      acc = fma(col[k].x, __shfl_sync(FULL, col[k].x, q), acc);
+      acc = fma(col[k].y, __shfl_sync(FULL, col[k].y, q), acc);
+      acc = fma(col[k].z, __shfl_sync(FULL, col[k].z, q), acc);
+    }
+    row[q] = acc;
+  }
+  // every lane gathers the packed lower triangle and the gradient
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    g[a] = __shfl_sync(FULL, gp, a);
+#pragma unroll
+    for (int b = 0; b <= a; ++b) jtj[tri(a, b)] = __shfl_sync(FULL, row[b], a);
+  }
+  return cost;
+}
+
+// gn_f64 with eval_lanes: one warp per candidate, every lane holding the
+// same iterate; the factorisation and the decisions run in every lane.
+template <int N>
+__device__ double gn_f64_lanes(const int (&kind)[N], const Rec<double>& rm, double (&prm)[2 * N],
+                               const v3<double>& A, const v3<double>& B, int max_iters, double mu, double stop,
+                               int lane) {
+  constexpr int Q = 2 * N, P = Q * (Q + 1) / 2;
+  double jtj[P], g[Q], dlt[Q], trial[Q], jt2[P], g2[Q];
+  double cost = (double)INFINITY;
+  double alpha = 1.0;
+  bool need_factor = true;
+#pragma unroll 1
+  for (int it = -1; it < 2 * max_iters; ++it) {
+    if (it >= 0) {
+      if (!(cost >= stop)) break;
+      if (need_factor) {
+        pin_unused<N, double>(kind, jtj, g);
+        cholesky<Q, double>(jtj, mu);
+        chol_solve<Q, double>(jtj, g, dlt);
+        double pred = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) pred = fma(-g[i], dlt[i], pred);
+        if (pred < 1e-3 * cost) break;
+        alpha = 1.0;
+        need_factor = false;
+      }
+#pragma unroll
+      for (int i = 0; i < Q; ++i) trial[i] = fma(alpha, dlt[i], prm[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) trial[i] = prm[i];
+    }
+    bool ok;
+    const double ct = eval_lanes<N>(kind, rm, trial, A, B, jt2, g2, ok, lane);
+    if (it < 0) {
+      if (!ok) return (double)INFINITY;
+      cost = ct;
+#pragma unroll
+      for (int i = 0; i < P; ++i) jtj[i] = jt2[i];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) g[i] = g2[i];
+      continue;
+    }
+    if (ok && ct < cost) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) prm[i] = trial[i];
+#pragma unroll
+      for (int i = 0; i < P; ++i) jtj[i] = jt2[i];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) g[i] = g2[i];
+      const bool stagnant = ct > 0.25 * cost;
+      cost = ct;
+      if (stagnant) break;
+      need_factor = true;
+    } else {
+      alpha *= 0.5;
+      if (alpha < 1.0 / 16.0) break;
+    }
+  }
+  return cost;
+}
+
 // One thread per listed candidate: up to refine_steps mixed steps (residual
 // and cost in float-float, Jacobian and solve in FP32) until the cost is
 // below 1e-24, extended by up to 6 steps while they still halve the cost.
@@ -1050,14 +1270,19 @@ __global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? 3 : 1)) k_refine(DevSce
   }
 }
 
-// The fallback of the refinement: Gauss-Newton (FP64 or float-float) for the queued
-// candidates, one candidate per warp (lane 0) so that the few long serial
-// solves run side by side on as many SM sub-partitions as there are.
-template <int N, bool F64>
+// The fallback of the refinement: Gauss-Newton (FP64 or float-float) for the
+// queued candidates, one candidate per warp so that the few long serial
+// solves run side by side on as many SM sub-partitions as there are.  MODE:
+// FB_F64_WARP (the default) FP64 with the evaluation spread over the warp's
+// lanes (eval_lanes); FB_F64 and FB_FF FP64 or float-float on lane 0 alone.
+enum { FB_FF = 0, FB_F64 = 1, FB_F64_WARP = 2 };
+
+template <int N, int MODE>
 __global__ void __launch_bounds__(32) k_refine_fb(DevScene sc, DevEnds ep, CandView cv, SolView out, SolveCfg cfg,
                                                   RefineList rl3) {
   constexpr int Q = 2 * N;
-  if (threadIdx.x != 0) return;
+  const int lane = (int)threadIdx.x;
+  if (MODE != FB_F64_WARP && lane != 0) return;
   int64_t end = cv.order_begin[N];
   if (end > cv.cap) end = cv.cap;
   int64_t begin = cv.order_begin[N - 1];
@@ -1074,7 +1299,29 @@ __global__ void __launch_bounds__(32) k_refine_fb(DevScene sc, DevEnds ep, CandV
 #pragma unroll
     for (int k = 0; k < N; ++k) kind[k] = __ldg(sc.kind + cd.ids[k]);
     const double c1 = out.cost[c];
-    if constexpr (F64) {
+    if constexpr (MODE == FB_F64_WARP) {
+      const v3<double> A = mk(ep.tx[3 * it_], ep.tx[3 * it_ + 1], ep.tx[3 * it_ + 2]);
+      const v3<double> B = mk(ep.rx[3 * ir_], ep.rx[3 * ir_ + 1], ep.rx[3 * ir_ + 2]);
+      // this lane's object (point lane >> 1); lanes past the sequence hold zeros
+      Rec<double> rm;
+#pragma unroll
+      for (int f = 0; f < 16; ++f) rm.v[f] = 0.0;
+      int id = -1;
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        if (k == (lane >> 1)) id = cd.ids[k];
+      if (id >= 0) rm = load_obj64(sc, id);
+      double T[Q];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) T[j] = out.T[(int64_t)j * out.cap + c];
+      const double c2 =
+          gn_f64_lanes<N>(kind, rm, T, A, B, cfg.fallback_iters, cfg.mu64, (double)REFINE_TARGET, lane);
+      if (lane == 0 && isfinite(c2) && c2 < c1) {
+#pragma unroll
+        for (int j = 0; j < Q; ++j) out.T[(int64_t)j * out.cap + c] = T[j];
+        out.cost[c] = c2;
+      }
+    } else if constexpr (MODE == FB_F64) {
       const v3<double> A = mk(ep.tx[3 * it_], ep.tx[3 * it_ + 1], ep.tx[3 * it_ + 2]);
       const v3<double> B = mk(ep.rx[3 * ir_], ep.rx[3 * ir_ + 1], ep.rx[3 * ir_ + 2]);
       Rec<double> rec[N];
@@ -1166,10 +1413,12 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
                                                                                cfg.prescreen ? rl2 : rl, rl3,   \
                                                                                ctx->counters + 20 + (N - 1));   \
       MPT_LAUNCH_CHECK();                                                                                      \
-      if (cfg.fallback_f64)                                                                                    \
-        k_refine_fb<N, true><<<ctx->sms * 4, 32, 0, s_>>>(sc, ep, cv, sv, cfg, rl3);                           \
+      if (cfg.fallback == FB_F64_WARP)                                                                         \
+        k_refine_fb<N, FB_F64_WARP><<<ctx->sms * 4, 32, 0, s_>>>(sc, ep, cv, sv, cfg, rl3);                    \
+      else if (cfg.fallback == FB_F64)                                                                         \
+        k_refine_fb<N, FB_F64><<<ctx->sms * 4, 32, 0, s_>>>(sc, ep, cv, sv, cfg, rl3);                         \
       else                                                                                                     \
-        k_refine_fb<N, false><<<ctx->sms * 4, 32, 0, s_>>>(sc, ep, cv, sv, cfg, rl3);                          \
+        k_refine_fb<N, FB_FF><<<ctx->sms * 4, 32, 0, s_>>>(sc, ep, cv, sv, cfg, rl3);                          \
       MPT_LAUNCH_CHECK();                                                                                      \
     }                                                                                                          \
   }
@@ -1198,7 +1447,7 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
   cfg.piece = (sch && sch->tile > 0) ? (sch->tile < 32 ? 32 : (sch->tile > GN_CHUNK ? GN_CHUNK : sch->tile)) : GN_CHUNK;
   cfg.fallback_iters = 2;  // at most 5 evaluations
   cfg.prescreen = (sch && sch->prescreen == 2) ? 0 : 1;
-  cfg.fallback_f64 = (sch && sch->fallback == 1) ? 0 : 1;
+  cfg.fallback = !sch ? FB_F64_WARP : sch->fallback == 1 ? FB_FF : sch->fallback == 3 ? FB_F64 : FB_F64_WARP;
   const double S = scene->d.scale;
   cfg.c_tol32 = 1e-12f;
   cfg.step_tol32 = (float)(1e-6 * S);

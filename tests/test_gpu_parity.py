@@ -272,6 +272,33 @@ def test_mixed_orders_single_launch_matches_per_order(mpt, ctx):
     assert torch.allclose(p1.X[:, :p1.n()], p2.X[:, :p2.n()], atol=1e-9, rtol=0)
 
 
+@pytest.mark.parametrize("name", ["urban_block", "curved"])
+def test_warp_fallback_equals_single_lane_fallback(mpt, ctx, name):
+    """The refinement's fallback with its FP64 evaluation spread over a warp
+    (the default) against the same Gauss-Newton on one lane: the same queued
+    candidates, the same valid paths, points within 1e-9 m (J^T J is summed
+    in another order)."""
+    if name == "urban_block":
+        sc, spec, order = S.urban_block(32), S.CONFIG_SPECS["urban_block"], 2
+    else:
+        sc, spec, order = S.curved_scene(), S.CONFIG_SPECS["curved"], 3
+    _, _, s1, p1 = gpu_trace(mpt, ctx, sc, order, spec, path_cap=1 << 21)
+    sched = mpt.schedule_struct(fallback=3)
+    _, _, s2, p2 = gpu_trace(mpt, ctx, sc, order, spec, schedule=sched, path_cap=1 << 21)
+    fb1 = (s1.status & mpt.PATH_FALLBACK) != 0
+    fb2 = (s2.status & mpt.PATH_FALLBACK) != 0
+    assert torch.equal(fb1, fb2)
+    n_fb = int(fb1.sum().item())
+    if name == "urban_block":
+        assert n_fb >= 50, n_fb
+    a = p1.cand[:p1.n()].cpu().numpy()
+    b = p2.cand[:p2.n()].cpu().numpy()
+    assert np.array_equal(a, b)
+    assert torch.allclose(p1.X[:, :p1.n()], p2.X[:, :p2.n()], atol=1e-9, rtol=0)
+    both = fb1 & torch.isfinite(s1.cost) & torch.isfinite(s2.cost) & (s1.cost < 1e-20) & (s2.cost < 1e-20)
+    print(f"{name}: {n_fb} fallback candidates, {int(both.sum().item())} converged in both")
+
+
 def test_cuda_graph_replay_matches_eager(mpt, ctx):
     sc = S.mixed_order_city()
     spec = S.CONFIG_SPECS["mixed_order"]
