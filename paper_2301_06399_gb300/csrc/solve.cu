@@ -1185,7 +1185,9 @@ __device__ double gn_f64_lanes(const int (&kind)[N], const Rec<double>& rm, doub
 // from the origin) and far below the acceptance threshold 1e-20.
 constexpr float REFINE_STOP = 1e-24f, REFINE_TARGET = 1e-22f;
 
-template <int N>
+// CURVED = false: scenes of planes and straight edges only (no paraboloid or
+// arc branches in the evaluation: shorter code, fewer registers).
+template <int N, bool CURVED>
 __global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? 3 : 1)) k_refine(DevScene sc, DevEnds ep, CandView cv,
                                                                         SolView out, SolveCfg cfg, RefineList rl,
                                                                         RefineList rl3, unsigned long long* cursor) {
@@ -1248,7 +1250,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK, (N <= 2 ? 3 : 1)) k_refine(DevSce
 #pragma unroll
             for (int j = 0; j < Q; ++j) T[j] = T[j] + ff(dlt[j]);
           }
-          cst = eval_path<N, ff, float, true>(kind, rec, T, A, B, jtj, g, ok);
+          cst = eval_path<N, ff, float, true, CURVED>(kind, rec, T, A, B, jtj, g, ok);
         }
         fallback = !ok || !(cst < target);
         // the fallback starts from what is written here: the mixed result,
@@ -1409,9 +1411,12 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
             sc, ep, ends32, cv, sv, rl, rl2, ctx->counters + 24 + (N - 1));                                    \
         MPT_LAUNCH_CHECK();                                                                                    \
       }                                                                                                        \
-      k_refine<N><<<grid_for(ctx, k_refine<N>, nullptr), SOLVE_BLOCK, 0, s_>>>(sc, ep, cv, sv, cfg,             \
-                                                                               cfg.prescreen ? rl2 : rl, rl3,   \
-                                                                               ctx->counters + 20 + (N - 1));   \
+      if (curved)                                                                                              \
+        k_refine<N, true><<<grid_for(ctx, k_refine<N, true>, nullptr), SOLVE_BLOCK, 0, s_>>>(                  \
+            sc, ep, cv, sv, cfg, cfg.prescreen ? rl2 : rl, rl3, ctx->counters + 20 + (N - 1));                 \
+      else                                                                                                     \
+        k_refine<N, false><<<grid_for(ctx, k_refine<N, false>, nullptr), SOLVE_BLOCK, 0, s_>>>(                \
+            sc, ep, cv, sv, cfg, cfg.prescreen ? rl2 : rl, rl3, ctx->counters + 20 + (N - 1));                 \
       MPT_LAUNCH_CHECK();                                                                                      \
       if (cfg.fallback == FB_F64_WARP)                                                                         \
         k_refine_fb<N, FB_F64_WARP><<<ctx->sms * 4, 32, 0, s_>>>(sc, ep, cv, sv, cfg, rl3);                    \
