@@ -52,7 +52,9 @@ struct GradOut {
   double obj[N];  // d/d offset of plane ids[m]; 0 for other kinds
 };
 
-template <int N>
+// CURVED = false: scenes of planes and straight edges only (no paraboloid or
+// arc branches: shorter code).
+template <int N, bool CURVED>
 __device__ bool grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, const double* Tc, double gL,
                          const double* gX, bool want_tx, bool want_rx, bool want_obj, GradOut<N>& o) {
   constexpr int Q = 2 * N;
@@ -74,7 +76,7 @@ __device__ bool grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, 
   // geometry
   PointT<S> pt[N];
 #pragma unroll
-  for (int k = 0; k < N; ++k) pt[k] = point_at<S, true>(kind[k], rec[k], prm[2 * k], prm[2 * k + 1]);
+  for (int k = 0; k < N; ++k) pt[k] = point_at<S, true, CURVED>(kind[k], rec[k], prm[2 * k], prm[2 * k + 1]);
   v3<S> u[N + 1];
   S il[N + 1];
 #pragma unroll
@@ -113,7 +115,7 @@ __device__ bool grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, 
   // normal matrix at the solution
   S jtj[Q * (Q + 1) / 2], g[Q];
   bool ok;
-  eval_path<N, S, S, true>(kind, rec, prm, A, B, jtj, g, ok);
+  eval_path<N, S, S, true, CURVED>(kind, rec, prm, A, B, jtj, g, ok);
 #pragma unroll
   for (int k = 0; k < N; ++k)
     if (is_edge(kind[k])) jtj[tri(2 * k + 1, 2 * k + 1)] = S(1);
@@ -131,12 +133,12 @@ __device__ bool grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, 
     inv_nn[k] = S(0);
     if (kind[k] == K_PLANE) {
       in[k].nh = rec[k].f3(12);
-    } else if (kind[k] == K_PARAB) {
+    } else if (CURVED && kind[k] == K_PARAB) {
       const S q2 = rec[k].v[14];
       const v3<S> nraw = axpy(-prm[2 * k + 1] * q2, rec[k].f3(4), axpy(-prm[2 * k] * q2, rec[k].f3(0), rec[k].f3(8)));
       inv_nn[k] = rsq(dot(nraw, nraw));
       in[k].nh = nraw * inv_nn[k];
-    } else if (kind[k] == K_LINE) {
+    } else if (!CURVED || kind[k] == K_LINE) {
       in[k].eh = rec[k].f3(4);
     } else {
       S sn, cs;
@@ -166,14 +168,14 @@ __device__ bool grad_one(const DevScene& sc, const DevEnds& ep, const Cand& cd, 
     v3<S> r = in[k].self(D[k]);
     if (k >= 1) r = r + in[k].prev(D[k - 1]);
     if (k + 1 < N) r = r + in[k].next(D[k + 1]);
-    if (kind[k] == K_PARAB) {
+    if (CURVED && kind[k] == K_PARAB) {
       // normal variation: 2 (<i, dn> n + <i, n> dn), dn from the parameters
       const S q2 = rec[k].v[14];
       const v3<S> craw = axpy(lam[2 * k + 1], rec[k].f3(4), rec[k].f3(0) * lam[2 * k]) * (-q2);
       const v3<S> dn = axpy(-dot(in[k].nh, craw), in[k].nh, craw) * inv_nn[k];
       r = axpy(S(2) * dot(in[k].ih, dn), in[k].nh, r);
       r = axpy(S(2) * curv_c[k], dn, r);
-    } else if (kind[k] == K_ARC) {
+    } else if (CURVED && kind[k] == K_ARC) {
       S sn, cs;
       sincos_(prm[2 * k], sn, cs);
       const v3<S> de = axpy(-sn, rec[k].f3(8), rec[k].f3(4) * (-cs));
@@ -253,7 +255,7 @@ struct GradView {
 // aggregated atomics together.
 // PTS: point weights given (the normal-matrix solve; few registers spare)
 // or not (explicit gradient only: a short kernel at full occupancy).
-template <int N, bool PTS>
+template <int N, bool PTS, bool CURVED>
 __global__ void __launch_bounds__(GRAD_BLOCK, (PTS ? (N <= 2 ? 3 : 1) : 4)) k_grad(DevScene sc, DevEnds ep,
                                                                                   GradView gv, double* g_tx,
                                                                                   double* g_rx, double* g_obj) {
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(GRAD_BLOCK, (PTS ? (N <= 2 ? 3 : 1) : 4)) k_gr
             for (int j = 0; j < 3 * N; ++j) gX[j] = gv.g_pts[(int64_t)j * gv.pcap + i];
             gxp = gX;
           }
-          have = grad_one<N>(sc, ep, cd, Tc, gv.g_len[i], gxp, g_tx != nullptr, g_rx != nullptr,
+          have = grad_one<N, CURVED>(sc, ep, cd, Tc, gv.g_len[i], gxp, g_tx != nullptr, g_rx != nullptr,
                              g_obj != nullptr, o);
         }
       }
@@ -311,19 +313,26 @@ int launch_grad(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
   // the orders are independent (their sums meet only in atomics): order 2
   // on the caller's stream, orders 1, 3, 4 on the context's auxiliary streams
   MPT_CUDA_TRY(fork_streams(ctx, st));
-#define MPT_GRAD(N, S)                                                                           \
-  {                                                                                              \
-    if (g_pts)                                                                                   \
-      k_grad<N, true><<<(unsigned)blocks, GRAD_BLOCK, 0, (S)>>>(scene->d, ep, gv, g_tx, g_rx, g_obj);  \
-    else                                                                                         \
-      k_grad<N, false><<<(unsigned)blocks, GRAD_BLOCK, 0, (S)>>>(scene->d, ep, gv, g_tx, g_rx, g_obj); \
-    MPT_LAUNCH_CHECK();                                                                          \
+  const bool curved = scene_curved(scene);
+#define MPT_GRAD_K(N, P, CV, S) k_grad<N, P, CV><<<(unsigned)blocks, GRAD_BLOCK, 0, (S)>>>(scene->d, ep, gv, g_tx, g_rx, g_obj)
+#define MPT_GRAD(N, S)                                         \
+  {                                                            \
+    if (g_pts && curved)                                       \
+      MPT_GRAD_K(N, true, true, S);                            \
+    else if (g_pts)                                            \
+      MPT_GRAD_K(N, true, false, S);                           \
+    else if (curved)                                           \
+      MPT_GRAD_K(N, false, true, S);                           \
+    else                                                       \
+      MPT_GRAD_K(N, false, false, S);                          \
+    MPT_LAUNCH_CHECK();                                        \
   }
   MPT_GRAD(2, st)
   MPT_GRAD(1, ctx->aux[0])
   MPT_GRAD(3, ctx->aux[1])
   MPT_GRAD(4, ctx->aux[2])
 #undef MPT_GRAD
+#undef MPT_GRAD_K
   MPT_CUDA_TRY(join_streams(ctx, st));
   return MPT_OK;
 }

@@ -221,6 +221,14 @@ struct mpt_scene {
   size_t alloc_bytes;      // size of `alloc`
 };
 
+// A scene holds a paraboloid or an arc edge (kernels for planes and
+// straight edges alone are instantiated without the curved branches).
+inline bool scene_curved(const mpt_scene* s) {
+  for (int i = 0; i < s->n_obj; ++i)
+    if (s->host_kind[i] == MPT_PARABOLOID || s->host_kind[i] == MPT_ARC_EDGE) return true;
+  return false;
+}
+
 #define MPT_CUDA_TRY(expr)                                                 \
   do {                                                                     \
     cudaError_t e_ = (expr);                                               \

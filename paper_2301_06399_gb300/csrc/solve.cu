@@ -1503,9 +1503,7 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
     k_ends_f32<<<(n_ends + 255) / 256, 256, 0, st>>>(ends->tx, ends->n_tx, ends->rx, ends->n_rx, ends32);
     MPT_LAUNCH_CHECK();
   }
-  bool curved = false;
-  for (int i = 0; i < scene->n_obj; ++i)
-    curved = curved || scene->host_kind[i] == MPT_PARABOLOID || scene->host_kind[i] == MPT_ARC_EDGE;
+  const bool curved = scene_curved(scene);
   switch (precision) {
     case MPT_FP64_PLAIN:
       return launch_prec<MPT_FP64_PLAIN>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, st);
