@@ -375,6 +375,10 @@ MPT_HD R eval_path(const int (&kind)[N], const Rec<R> (&rec)[N], const R (&prm)[
 
 // Cholesky factorisation of the packed Q x Q matrix in place (lower), with
 // relative diagonal damping mu.  Returns false when a pivot is not positive.
+// Every loop runs a fixed Q trips under a compile-time guard, so that full
+// unrolling leaves only constant indices (a trip count that depends on an
+// outer index was not unrolled at Q = 6, 8, and the matrix went to local
+// memory).
 template <int Q, class J>
 MPT_HD bool cholesky(J* a, J mu) {
   bool ok = true;
@@ -382,16 +386,19 @@ MPT_HD bool cholesky(J* a, J mu) {
   for (int j = 0; j < Q; ++j) {
     J d = a[tri(j, j)];
 #pragma unroll
-    for (int k = 0; k < j; ++k) d = fma_(-a[tri(j, k)], a[tri(j, k)], d);
+    for (int k = 0; k < Q; ++k)
+      if (k < j) d = fma_(-a[tri(j, k)], a[tri(j, k)], d);
     d = d + mu * a[tri(j, j)] + J(1e-30f);
     ok = ok && (d > J(0));
     const J inv = rsq(d > J(0) ? d : J(1));
     a[tri(j, j)] = inv;  // store 1/L_jj
 #pragma unroll
-    for (int i = j + 1; i < Q; ++i) {
+    for (int i = 0; i < Q; ++i) {
+      if (i <= j) continue;
       J s = a[tri(i, j)];
 #pragma unroll
-      for (int k = 0; k < j; ++k) s = fma_(-a[tri(i, k)], a[tri(j, k)], s);
+      for (int k = 0; k < Q; ++k)
+        if (k < j) s = fma_(-a[tri(i, k)], a[tri(j, k)], s);
       a[tri(i, j)] = s * inv;
     }
   }
@@ -406,14 +413,17 @@ MPT_HD void chol_solve(const J* a, const J* g, J* x) {
   for (int i = 0; i < Q; ++i) {
     J s = -g[i];
 #pragma unroll
-    for (int k = 0; k < i; ++k) s = fma_(-a[tri(i, k)], y[k], s);
+    for (int k = 0; k < Q; ++k)
+      if (k < i) s = fma_(-a[tri(i, k)], y[k], s);
     y[i] = s * a[tri(i, i)];
   }
 #pragma unroll
-  for (int i = Q - 1; i >= 0; --i) {
+  for (int r = 0; r < Q; ++r) {
+    const int i = Q - 1 - r;
     J s = y[i];
 #pragma unroll
-    for (int k = i + 1; k < Q; ++k) s = fma_(-a[tri(k, i)], x[k], s);
+    for (int k = 0; k < Q; ++k)
+      if (k > i) s = fma_(-a[tri(k, i)], x[k], s);
     x[i] = s * a[tri(i, i)];
   }
 }
