@@ -710,6 +710,32 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_mixed(DevScene sc, DevEnds e
 // list that k_refine processes.  Paraboloid occluders never reject here.
 constexpr float CLEAR_M = 0.25f;
 
+// seg_box on paired FP32 instructions, for boxes stored as (lo.x, hi.x,
+// lo.y, hi.y), (lo.z, hi.z, -, -): per axis one paired add and one paired
+// multiply give ((lo - A) inv, (hi - A) inv), the same roundings as seg_box,
+// so the same decisions; the segment's pairs are formed once per segment.
+struct SegPairs {
+  float2 nax, nay, naz, ivx, ivy, ivz;
+};
+__device__ __forceinline__ SegPairs seg_pairs(const v3<float>& A, const v3<float>& inv) {
+  SegPairs p;
+  p.nax = bc(-A.x);
+  p.nay = bc(-A.y);
+  p.naz = bc(-A.z);
+  p.ivx = bc(inv.x);
+  p.ivy = bc(inv.y);
+  p.ivz = bc(inv.z);
+  return p;
+}
+__device__ __forceinline__ bool seg_box2(const SegPairs& p, const float4& b0, const float4& b1) {
+  const float2 x = f2mul(f2add(make_float2(b0.x, b0.y), p.nax), p.ivx);
+  const float2 y = f2mul(f2add(make_float2(b0.z, b0.w), p.nay), p.ivy);
+  const float2 z = f2mul(f2add(make_float2(b1.x, b1.y), p.naz), p.ivz);
+  const float t0 = fmaxf(fmaxf(fminf(x.x, x.y), fminf(y.x, y.y)), fmaxf(fminf(z.x, z.y), 0.f));
+  const float t1 = fminf(fminf(fmaxf(x.x, x.y), fmaxf(y.x, y.y)), fminf(fmaxf(z.x, z.y), 1.f));
+  return t0 <= t1;
+}
+
 // Occluder o (staged in shared memory: fields 0-3 of the FP32 records, then
 // the boxes lo (w = kind) and hi) crosses segment AB with a clearance of
 // CLEAR_M everywhere.
@@ -743,10 +769,19 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
   if (n > end - begin) n = end - begin;
   if (n <= 0) return;  // the whole block
   const int no = sc.n_occ, ng = sc.n_grp;
-  for (int q = threadIdx.x; q < 6 * no + 2 * ng; q += blockDim.x)
-    occ_sm[q] = q < 4 * no ? __ldg(sc.c32 + q) : q < 6 * no ? __ldg(sc.cbox + (q - 4 * no)) : __ldg(sc.gbox + (q - 6 * no));
+  // occluder records and boxes as they are; the group boxes interleaved as
+  // pairs for the paired slab test: (lo.x, hi.x, lo.y, hi.y), (lo.z, hi.z, 0, 0)
+  for (int q = threadIdx.x; q < 6 * no + 2 * ng; q += blockDim.x) {
+    if (q < 6 * no) {
+      occ_sm[q] = q < 4 * no ? __ldg(sc.c32 + q) : __ldg(sc.cbox + (q - 4 * no));
+    } else {
+      const int g = (q - 6 * no) >> 1;
+      const float4 lo = __ldg(sc.gbox + g), hi = __ldg(sc.gbox + ng + g);
+      occ_sm[q] = ((q - 6 * no) & 1) ? make_float4(lo.z, hi.z, 0.f, 0.f) : make_float4(lo.x, hi.x, lo.y, hi.y);
+    }
+  }
   __syncthreads();
-  const float4* grp_sm = occ_sm + 6 * no;  // [2][ng]
+  const float4* grp_sm = occ_sm + 6 * no;  // [ng][2], interleaved
   const unsigned lane = threadIdx.x & 31;
   // warps claim 32 list entries at a time
   for (;;) {
@@ -788,10 +823,11 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_vis_prescreen(DevScene sc, DevE
         if (!test || blocked) continue;
         const v3<float> Af = P[j], Bf = P[j + 1];
         const v3<float> inv = mk(1.0f / (Bf.x - Af.x), 1.0f / (Bf.y - Af.y), 1.0f / (Bf.z - Af.z));
+        const SegPairs sp = seg_pairs(Af, inv);
         for (int g0 = 0; g0 < ng && !blocked; g0 += 32) {
           const int gn = ng - g0 < 32 ? ng - g0 : 32;
           uint32_t gm = 0;
-          for (int q = 0; q < gn; ++q) gm |= (uint32_t)seg_box(Af, inv, grp_sm[g0 + q], grp_sm[ng + g0 + q]) << q;
+          for (int q = 0; q < gn; ++q) gm |= (uint32_t)seg_box2(sp, grp_sm[2 * (g0 + q)], grp_sm[2 * (g0 + q) + 1]) << q;
           while (gm != 0 && !blocked) {
             const int gi = g0 + __ffs(gm) - 1;
             gm &= gm - 1;
