@@ -10,6 +10,7 @@
 // the FLOP model of the kernels.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 
 #if defined(__CUDACC__)
@@ -45,9 +46,45 @@ MPT_HD double rsq(double x) {
   return y;
 }
 
+// sin and cos of an FP32 argument by Cody and Waite's method ("Software
+// Manual for the Elementary Functions", 1980): x = k pi/2 + r with
+// k = rint(2x/pi) and |r| <= pi/4, pi/2 split over three floats and taken off
+// with fused multiply-adds; then the Taylor series of sin r to r^9 and of
+// cos r to r^10 (truncation below 3e-9 on |r| <= pi/4), and the quadrant
+// k mod 4.  The device uses it instead of the library's sincosf: that
+// carries a long path for huge arguments, and inlined at every arc
+// evaluation it kept the curved solvers waiting on instruction fetch (19% of
+// the curved scene's solve).  The reduction stays accurate for |x| up to
+// ~1e5 (arc parameters that large only occur on diverging iterates).
+// Constants: P1 + P2 + P3 = pi/2 (each the float nearest the remainder),
+// 2/pi and 1/n! rounded to float.
+MPT_HD void sincos_cw(float x, float& s, float& c) {
+  const float k = rintf(x * 0.636619747f);
+  float r = fmaf(-k, 1.57079637f, x);
+  r = fmaf(-k, -4.37113883e-8f, r);
+  r = fmaf(-k, -1.71512451e-15f, r);
+  const float r2 = r * r;
+  float ps = fmaf(r2, 2.75573188e-6f, -1.98412701e-4f);
+  ps = fmaf(r2, ps, 8.33333377e-3f);
+  ps = fmaf(r2, ps, -1.66666672e-1f);
+  const float sr = fmaf(r * r2, ps, r);
+  float pc = fmaf(r2, -2.75573200e-7f, 2.48015876e-5f);
+  pc = fmaf(r2, pc, -1.38888892e-3f);
+  pc = fmaf(r2, pc, 4.16666679e-2f);
+  pc = fmaf(r2, pc, -0.5f);
+  const float cr = fmaf(r2, pc, 1.0f);
+  // quadrant: 0 (s, c), 1 (c, -s), 2 (-s, -c), 3 (-c, s); a NaN k leaves
+  // NaN in r and in both results
+  const float qf = k - 4.0f * floorf(0.25f * k);
+  const int q = (qf >= 0.0f && qf < 4.0f) ? (int)qf : 0;
+  const float s0 = (q & 1) ? cr : sr, c0 = (q & 1) ? sr : cr;
+  s = (q & 2) ? -s0 : s0;
+  c = (q == 1 || q == 2) ? -c0 : c0;
+}
+
 MPT_HD void sincos_(float x, float& s, float& c) {
 #if defined(__CUDA_ARCH__)
-  sincosf(x, &s, &c);
+  sincos_cw(x, s, c);
 #else
   s = sinf(x);
   c = cosf(x);

@@ -16,7 +16,8 @@
 // the visibility prescreen does not reject are refined with mixed steps
 // (residual and cost in float-float, Jacobian in FP32); ill-conditioned ones
 // (near object creases) go on to a full Gauss-Newton solve (k_refine_fb, in
-// FP64 by default, float-float on request).
+// FP64 spread over the lanes of a warp by default; FP64 or float-float on one
+// lane on request).
 // Every other candidate is rejected by validation whatever its last digits,
 // so it keeps its FP32 result.
 //
@@ -929,10 +930,12 @@ __device__ ff gn_ff(const int (&kind)[N], const Rec<ff> (&rec)[N], ff (&prm)[2 *
   return cost;
 }
 
-// The fallback in FP64 arithmetic (the default), with the rules of gn_ff:
-// the FP64 code is a fraction of the length of the float-float one, which
-// matters for a lone serial chain that otherwise waits on instruction fetch
-// (measured: the order-2 fallback of the urban block 59 us faster).
+// The fallback in FP64 arithmetic on one lane (schedule fallback = 3), with
+// the rules of gn_ff: the FP64 code is a fraction of the length of the
+// float-float one, which matters for a lone serial chain that otherwise waits
+// on instruction fetch (measured: the order-2 fallback of the urban block
+// 59 us faster than float-float).  The default spreads the same iteration
+// over a warp (gn_f64_lanes below).
 template <int N>
 __device__ double gn_f64(const int (&kind)[N], const Rec<double> (&rec)[N], double (&prm)[2 * N], const v3<double>& A,
                          const v3<double>& B, int max_iters, double mu, double stop) {
