@@ -197,6 +197,11 @@ typedef struct {
                              0 library default (2), 1 float-float on one lane,
                              2 FP64 with each candidate's evaluation spread over
                              the lanes of a warp, 3 FP64 on one lane */
+  int32_t warp_orders;    /* bit n-1 set: the FP32 iterations of order n run one
+                             candidate per warp, the evaluation spread over its
+                             lanes (same minimiser and stopping rules); 0 (the
+                             default): one candidate per lane for every order.
+                             Applies to per-order launches (mixed_orders = 0) */
 } mpt_schedule;
 
 /* Compacted valid paths (caller-owned device buffers). */
@@ -313,8 +318,10 @@ int mpt_image_method(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* 
 /* Autotuner of mpt_solve's schedule for one workload (the batching of
  * Algorithm 1's loop over candidates and starts; the paper has no
  * counterpart).  Times mpt_solve on `cand` with `precision` under schedules
- * that differ only in knobs that leave every valid path unchanged (tile,
- * refill_min, blocks_per_sm, mixed_orders, prescreen; the iteration cap is
+ * that differ only in knobs that leave the valid paths unchanged (tile,
+ * refill_min, blocks_per_sm, mixed_orders and prescreen give bit-identical
+ * solutions; warp_orders sums the normal equations in another order and
+ * gives the same valid paths on every workload tested; the iteration cap is
  * part of the method and is not searched): a coordinate descent from the
  * defaults, two sweeps, each schedule timed with CUDA events as the best of
  * two solves.  *best receives the fastest schedule (pass it to mpt_solve),

@@ -1014,24 +1014,25 @@ __device__ double gn_f64(const int (&kind)[N], const Rec<double> (&rec)[N], doub
 // branches.  Lanes with no role compute values nobody reads.
 // Every shuffle below runs in all 32 lanes (none sits in a branch); source
 // lanes outside the warp are clamped and their values discarded.
-__device__ __forceinline__ v3<double> shfl3(const v3<double>& v, int src) {
+template <class R>
+__device__ __forceinline__ v3<R> shfl3(const v3<R>& v, int src) {
   src = src < 0 ? 0 : (src > 31 ? 31 : src);
   return mk(__shfl_sync(FULL, v.x, src), __shfl_sync(FULL, v.y, src), __shfl_sync(FULL, v.z, src));
 }
-__device__ __forceinline__ double shfl1(double v, int src) {
+template <class R>
+__device__ __forceinline__ R shfl1(R v, int src) {
   src = src < 0 ? 0 : (src > 31 ? 31 : src);
   return __shfl_sync(FULL, v, src);
 }
 
-template <int N>
-__device__ double eval_lanes(const int (&kind)[N], const Rec<double>& rm, const double (&prm)[2 * N],
-                             const v3<double>& A, const v3<double>& B, double* jtj, double* g, bool& ok,
-                             int lane) {
+template <int N, class R = double, bool CURVED = true>
+__device__ R eval_lanes(const int (&kind)[N], const Rec<R>& rm, const R (&prm)[2 * N], const v3<R>& A,
+                        const v3<R>& B, R* jtj, R* g, bool& ok, int lane) {
   constexpr int Q = 2 * N;
   const int m = lane >> 1, j = lane & 1;
   // this lane's point: object m, parameters (s, t) = prm[2m], prm[2m + 1]
   int km = K_PLANE;
-  double s = 0.0, t = 0.0;
+  R s = R(0), t = R(0);
 #pragma unroll
   for (int k = 0; k < N; ++k)
     if (k == m) {
@@ -1039,107 +1040,107 @@ __device__ double eval_lanes(const int (&kind)[N], const Rec<double>& rm, const 
       s = prm[2 * k];
       t = prm[2 * k + 1];
     }
-  const PointT<double> pt = point_at<double, true, true>(km, rm, s, t);
+  const PointT<R> pt = point_at<R, true, CURVED>(km, rm, s, t);
   // segment m: unit vector u and inverse length il (lanes 2m + 1)
-  const v3<double> Xprev = shfl3(pt.X, 2 * m - 2);
-  const v3<double> Xa = m == 0 ? A : Xprev;
-  const v3<double> Xb = m == N ? B : pt.X;
-  const v3<double> d = Xb - Xa;
-  const double l2 = dot(d, d);
-  const double il = rsq(l2);
-  const v3<double> u = d * il;
+  const v3<R> Xprev = shfl3(pt.X, 2 * m - 2);
+  const v3<R> Xa = m == 0 ? A : Xprev;
+  const v3<R> Xb = m == N ? B : pt.X;
+  const v3<R> d = Xb - Xa;
+  const R l2 = dot(d, d);
+  const R il = rsq(l2);
+  const v3<R> u = d * il;
   const bool seg_lane = (j == 1) && (m <= N);
-  ok = __ballot_sync(FULL, seg_lane && !(l2 > 0.0)) == 0u;
+  ok = __ballot_sync(FULL, seg_lane && !(l2 > R(0))) == 0u;
   // interaction m (lanes 2m): ih = u_m, rh = u_{m+1}
-  const v3<double> ih = shfl3(u, 2 * m + 1), rh = shfl3(u, 2 * m + 3);
-  v3<double> ax = mk(0.0, 0.0, 0.0), de = ax, rho = ax;  // axis: normal or edge direction
-  double c = 0.0, inv_nn = 0.0;
+  const v3<R> ih = shfl3(u, 2 * m + 1), rh = shfl3(u, 2 * m + 3);
+  v3<R> ax = mk(R(0), R(0), R(0)), de = ax, rho = ax;  // axis: normal or edge direction
+  R c = R(0), inv_nn = R(0);
   if (!is_edge(km)) {
-    if (km == K_PLANE) {
+    if (!CURVED || km == K_PLANE) {
       ax = rm.f3(12);
     } else {
-      const double q2 = rm.v[14];
-      const v3<double> nraw = axpy(-t * q2, rm.f3(4), axpy(-s * q2, rm.f3(0), rm.f3(8)));
+      const R q2 = rm.v[14];
+      const v3<R> nraw = axpy(-t * q2, rm.f3(4), axpy(-s * q2, rm.f3(0), rm.f3(8)));
       inv_nn = rsq(dot(nraw, nraw));
       ax = nraw * inv_nn;
     }
     c = dot(ih, ax);
-    rho = axpy(2.0 * c, ax, rh - ih);
+    rho = axpy(R(2) * c, ax, rh - ih);
   } else {
-    if (km == K_LINE) {
+    if (!CURVED || km == K_LINE) {
       ax = rm.f3(4);
     } else {
-      double sn, cs;
+      R sn, cs;
       sincos_(s, sn, cs);
       ax = axpy(cs, rm.f3(8), rm.f3(4) * (-sn));
       de = axpy(-sn, rm.f3(8), rm.f3(4) * (-cs));
     }
     rho.x = dot(ih, ax) - dot(rh, ax);
   }
-  const double part = fma(rho.x, rho.x, fma(rho.y, rho.y, rho.z * rho.z));
-  double cost = 0.0;
+  const R part = fma_(rho.x, rho.x, fma_(rho.y, rho.y, rho.z * rho.z));
+  R cost = R(0);
 #pragma unroll
   for (int k = 0; k < N; ++k) cost += __shfl_sync(FULL, part, 2 * k);
   // Jacobian column of this lane's slot (point m, tangent j); an edge's
   // second slot is unused (zero column, pinned by the caller)
   const bool live = (m < N) && !(j == 1 && is_edge(km));
-  const v3<double> w = j == 0 ? pt.w0 : pt.w1;
-  const v3<double> ui = ih, uo = rh;
-  const double li = shfl1(il, 2 * m + 1), lo = shfl1(il, 2 * m + 3);
-  const v3<double> PiW = axpy(-dot(ui, w), ui, w) * li;
-  const v3<double> PrW = axpy(-dot(uo, w), uo, w) * lo;
+  const v3<R> w = j == 0 ? pt.w0 : pt.w1;
+  const v3<R> ui = ih, uo = rh;
+  const R li = shfl1(il, 2 * m + 1), lo = shfl1(il, 2 * m + 3);
+  const v3<R> PiW = axpy(-dot(ui, w), ui, w) * li;
+  const v3<R> PrW = axpy(-dot(uo, w), uo, w) * lo;
   // own interaction m: the lane 2m values (this lane's own when j == 0)
-  const v3<double> ax_o = shfl3(ax, 2 * m), de_o = shfl3(de, 2 * m), rho_o = shfl3(rho, 2 * m);
-  const double c_o = shfl1(c, 2 * m), inn_o = shfl1(inv_nn, 2 * m);
+  const v3<R> ax_o = shfl3(ax, 2 * m), de_o = shfl3(de, 2 * m), rho_o = shfl3(rho, 2 * m);
+  const R c_o = shfl1(c, 2 * m), inn_o = shfl1(inv_nn, 2 * m);
   // neighbours m - 1 and m + 1
-  const v3<double> ax_p = shfl3(ax, 2 * m - 2), rho_p = shfl3(rho, 2 * m - 2);
-  const v3<double> ax_n = shfl3(ax, 2 * m + 2), rho_n = shfl3(rho, 2 * m + 2);
+  const v3<R> ax_p = shfl3(ax, 2 * m - 2), rho_p = shfl3(rho, 2 * m - 2);
+  const v3<R> ax_n = shfl3(ax, 2 * m + 2), rho_n = shfl3(rho, 2 * m + 2);
   int kp = K_PLANE, kn = K_PLANE;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     if (k + 1 == m) kp = kind[k];
     if (k == m + 1) kn = kind[k];
   }
-  const v3<double> zero = mk(0.0, 0.0, 0.0);
-  v3<double> cp = zero, co = zero, cn = zero;  // column blocks on interactions m-1, m, m+1
+  const v3<R> zero = mk(R(0), R(0), R(0));
+  v3<R> cp = zero, co = zero, cn = zero;  // column blocks on interactions m-1, m, m+1
   if (live) {
     // interaction m - 1 sees this point as its next one: d rho / dX = Pi_m w
-    if (m >= 1) cp = is_edge(kp) ? mk(-dot(ax_p, PiW), 0.0, 0.0) : PiW;
+    if (m >= 1) cp = is_edge(kp) ? mk(-dot(ax_p, PiW), R(0), R(0)) : PiW;
     // interaction m + 1 sees it as its previous one: H_{m+1}(Pr_m w)
-    if (m + 1 < N) cn = is_edge(kn) ? mk(-dot(ax_n, PrW), 0.0, 0.0) : axpy(-2.0 * dot(ax_n, PrW), ax_n, PrW);
+    if (m + 1 < N) cn = is_edge(kn) ? mk(-dot(ax_n, PrW), R(0), R(0)) : axpy(-R(2) * dot(ax_n, PrW), ax_n, PrW);
     if (!is_edge(km)) {
-      co = -(PrW + axpy(-2.0 * dot(ax_o, PiW), ax_o, PiW));
-      if (km == K_PARAB) {
-        const double q2 = rm.v[14];
-        const v3<double> craw = (j == 0 ? rm.f3(0) : rm.f3(4)) * (-q2);
-        const v3<double> dn = axpy(-dot(ax_o, craw), ax_o, craw) * inn_o;
-        co = axpy(2.0 * dot(ih, dn), ax_o, co);
-        co = axpy(2.0 * c_o, dn, co);
+      co = -(PrW + axpy(-R(2) * dot(ax_o, PiW), ax_o, PiW));
+      if (CURVED && km == K_PARAB) {
+        const R q2 = rm.v[14];
+        const v3<R> craw = (j == 0 ? rm.f3(0) : rm.f3(4)) * (-q2);
+        const v3<R> dn = axpy(-dot(ax_o, craw), ax_o, craw) * inn_o;
+        co = axpy(R(2) * dot(ih, dn), ax_o, co);
+        co = axpy(R(2) * c_o, dn, co);
       }
     } else {
-      double v = dot(ax_o, PiW) + dot(ax_o, PrW);
-      if (km == K_ARC) v = v + dot(ih - rh, de_o);
-      co = mk(v, 0.0, 0.0);
+      R v = dot(ax_o, PiW) + dot(ax_o, PrW);
+      if (CURVED && km == K_ARC) v = v + dot(ih - rh, de_o);
+      co = mk(v, R(0), R(0));
     }
   }
-  double gp = dot(co, rho_o);
+  R gp = dot(co, rho_o);
   if (m >= 1) gp += dot(cp, rho_p);
   if (m + 1 < N) gp += dot(cn, rho_n);
   // the column over every interaction (zero away from m-1 .. m+1)
-  v3<double> col[N];
+  v3<R> col[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) col[k] = (k + 1 == m) ? cp : (k == m) ? co : (k == m + 1) ? cn : zero;
   // row of J^T J: <col_L, col_q> over the interactions where column q lives
-  double row[Q];
+  R row[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    double acc = 0.0;
+    R acc = R(0);
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       if (k < (q >> 1) - 1 || k > (q >> 1) + 1) continue;
-      acc = fma(col[k].x, __shfl_sync(FULL, col[k].x, q), acc);
-      acc = fma(col[k].y, __shfl_sync(FULL, col[k].y, q), acc);
-      acc = fma(col[k].z, __shfl_sync(FULL, col[k].z, q), acc);
+      acc = fma_(col[k].x, __shfl_sync(FULL, col[k].x, q), acc);
+      acc = fma_(col[k].y, __shfl_sync(FULL, col[k].y, q), acc);
+      acc = fma_(col[k].z, __shfl_sync(FULL, col[k].z, q), acc);
     }
     row[q] = acc;
   }
@@ -1213,6 +1214,200 @@ __device__ double gn_f64_lanes(const int (&kind)[N], const Rec<double>& rm, doub
     }
   }
   return cost;
+}
+
+// --------------------------------------------------- warp-per-path solver --
+// The minimiser of gn_warp (Gauss-Newton on Eq. 15, the same backtracking
+// search, stopping rules and FP32 tolerances) with one warp per candidate:
+// the evaluation is spread over the lanes as in eval_lanes (lane L: point
+// L/2 and its tangent L%2, segment, interaction) and every lane holds the
+// same iterate, factorisation and decisions (the values that steer the
+// iteration are gathered in the same order in every lane).  A schedule
+// option (mpt_schedule.warp_orders) for solves whose lanes would diverge
+// most in the one-lane form; each candidate's iterations cost about four
+// times the issue slots there, so the one-lane solver is the default.
+// Warps claim 32 candidates at a time, one record per lane, and walk them.
+template <int N, int PREC, bool CURVED>
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_warp(DevScene sc, DevEnds ep, const float4* ends32, CandView cv,
+                                                        SolView out, SolveCfg cfg, unsigned long long* counter,
+                                                        RefineList rl) {
+  constexpr int Q = 2 * N, P = Q * (Q + 1) / 2;
+  const int lane = (int)(threadIdx.x & 31);
+  int64_t end = cv.order_begin[N];
+  if (end > cv.cap) end = cv.cap;
+  int64_t begin = cv.order_begin[N - 1];
+  if (begin > end) begin = end;
+  const float c_tol = cfg.c_tol32, step_tol = cfg.step_tol32, mu = cfg.mu32;
+  const float diverge = (float)cfg.diverge;
+  for (;;) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(counter, 32ull);
+    b = __shfl_sync(FULL, b, 0);
+    const int64_t base = begin + (int64_t)b;
+    if (base >= end) break;
+    const int len = end - base < 32 ? (int)(end - base) : 32;
+    const uint4 mine = lane < len ? __ldg(cv.rec + base + lane) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll 1
+    for (int i = 0; i < len; ++i) {
+      const int64_t c = base + i;
+      uint4 rr;
+      rr.x = __shfl_sync(FULL, mine.x, i);
+      rr.y = __shfl_sync(FULL, mine.y, i);
+      rr.z = __shfl_sync(FULL, mine.z, i);
+      rr.w = __shfl_sync(FULL, mine.w, i);
+      // a record of this order whose objects and endpoints exist
+      bool valid = (int)(rr.w & 0xFFu) == N;
+      int ids[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        ids[k] = (int)(((k < 2 ? rr.y : rr.z) >> (16 * (k & 1))) & 0xFFFFu);
+        valid = valid && ids[k] < sc.n_obj;
+      }
+      int it_, ir_;
+      pair_ends(ep, rr.x, it_, ir_);
+      valid = valid && it_ < ep.n_tx && ir_ < ep.n_rx;
+      if (!valid) {
+        if (lane == 0) {
+          out.cost[c] = (double)INFINITY;
+          out.status[c] = (uint8_t)MPT_PATH_NONFINITE;
+          out.iters[c] = 0;
+          out.evals[c] = 0;
+        }
+        continue;
+      }
+      int kind[N];
+      float lm_ratio = cfg.localmin_ratio_planar;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        kind[k] = __ldg(sc.kind + ids[k]);
+        if (CURVED && (kind[k] == K_PARAB || kind[k] == K_ARC)) lm_ratio = cfg.localmin_ratio;
+      }
+      // this lane's object (point lane / 2); lanes past the sequence hold zeros
+      Rec<float> rm;
+#pragma unroll
+      for (int f = 0; f < 16; ++f) rm.v[f] = 0.f;
+      int own = -1, km = K_PLANE;
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        if (k == (lane >> 1)) {
+          own = ids[k];
+          km = kind[k];
+        }
+      if (own >= 0) rm = load_obj32a(sc, own);
+      const v3<float> A = load_end<float>(ep.tx, ends32, it_);
+      const v3<float> B = load_end<float>(ep.rx, ends32 + ep.n_tx, ir_);
+      // initial guess (Algorithm 1, random_guess): lane 2k makes object k's
+      uint64_t packed = 0;
+      if constexpr (CURVED) {
+        packed = (uint64_t)rr.y | ((uint64_t)rr.z << 32);
+        if constexpr (N < 4) packed |= ~0ull << (16 * (N < 4 ? N : 0));
+      }
+      float s0 = 0.f, t0 = 0.f;
+      if ((lane & 1) == 0 && own >= 0)
+        init_params<float, CURVED>(km, rm, (lane < N) ? A : B, cv.init_seed, rr.x, packed, (int)((rr.w >> 8) & 0xFFu),
+                                   lane >> 1, s0, t0);
+      float trial[Q], prm[Q], dlt[Q], jtj[P], g[Q];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        trial[2 * k] = __shfl_sync(FULL, s0, 2 * k);
+        trial[2 * k + 1] = __shfl_sync(FULL, t0, 2 * k);
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) prm[q] = dlt[q] = 0.f;
+      float cost = 0.f, alpha = 1.f;
+      int iters = 0, evals = 0, done = -1;
+      bool fresh = true;
+#pragma unroll 1
+      for (;;) {
+        bool ok;
+        const float ct = eval_lanes<N, float, CURVED>(kind, rm, trial, A, B, jtj, g, ok, lane);
+        ++evals;
+        bool factor = false;
+        if (fresh) {
+          fresh = false;
+#pragma unroll
+          for (int q = 0; q < Q; ++q) prm[q] = trial[q];
+          cost = ct;
+          if (!(ok && isfinite(ct))) done = MPT_PATH_NONFINITE;
+          else if (cost < c_tol) done = MPT_PATH_CONVERGED;
+          else factor = true;
+        } else if (ok && ct < cost) {
+          float smax = 0.f, pmax = 0.f;
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            smax = fmaxf(smax, fabsf(trial[q] - prm[q]));
+            prm[q] = trial[q];
+            pmax = fmaxf(pmax, fabsf(prm[q]));
+          }
+          cost = ct;
+          ++iters;
+          if (!(pmax <= diverge)) done = MPT_PATH_DIVERGED;
+          else if (cost < c_tol || smax < step_tol) done = MPT_PATH_CONVERGED;
+          else if (iters >= cfg.max_iters) done = MPT_PATH_MAXITER;
+          else factor = true;
+        } else {
+          alpha = alpha * 0.5f;
+          if (alpha < cfg.min_alpha) done = MPT_PATH_STALLED;
+        }
+        if (done < 0 && evals >= cfg.max_evals) done = MPT_PATH_MAXITER;
+        if (factor && done < 0) {
+          pin_unused<N, float>(kind, jtj, g);
+          cholesky<Q, float>(jtj, mu);
+          chol_solve<Q, float>(jtj, g, dlt);
+          alpha = 1.f;
+          // local minimum with non-zero residual (as in gn_warp)
+          float pred = 0.f;
+#pragma unroll
+          for (int q = 0; q < Q; ++q) pred = fmaf(-g[q], dlt[q], pred);
+          if (iters >= 2 && cost > cfg.localmin_cost && pred < lm_ratio * cost) done = MPT_PATH_STALLED;
+        }
+        if (done >= 0) break;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) trial[q] = fmaf(alpha, dlt[q], prm[q]);
+      }
+      // ---- result: lane q writes slot q, lane 0 the rest
+      int status = done;
+      bool pass = false;
+      if (PREC == MPT_FP32_FP64REFINE) {
+        float sq = 0.f, tq = 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          if (k == (lane >> 1)) {
+            sq = prm[2 * k];
+            tq = prm[2 * k + 1];
+          }
+        const bool inb = !((lane & 1) == 0 && own >= 0) ||
+                         in_bounds_margin<float>(km, rm, sq, tq, cfg.prescreen_margin);
+        pass = __all_sync(FULL, inb) && isfinite(cost) && cost < cfg.prescreen_cost && done != MPT_PATH_DIVERGED;
+        if (!pass) status |= MPT_PATH_PRESCREENED;
+      }
+      float mine_q = 0.f;
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if (q == lane) mine_q = prm[q];
+      if (lane < Q) {
+        out.T[(int64_t)lane * out.cap + c] = to_f64(mine_q);
+        if (out.T32 != nullptr) out.T32[(int64_t)lane * out.cap + c] = mine_q;
+      }
+      if (lane == 0) {
+        out.cost[c] = to_f64(cost);
+        out.status[c] = (uint8_t)status;
+        out.iters[c] = (uint8_t)min(iters, 255);
+        out.evals[c] = (uint8_t)min(evals, 255);
+      }
+      if (PREC == MPT_FP32_FP64REFINE && pass) {
+        unsigned long long pos = 0;
+        if (lane == 0) pos = atomicAdd(rl.count + (N - 1), 1ull);
+        pos = __shfl_sync(FULL, pos, 0);
+        const int64_t at = begin + (int64_t)pos;
+        if (lane == 0) {
+          rl.idx[at] = (int32_t)(c - begin) | (cost < PRESCREEN_VIS_COST ? RL_VIS : 0);
+          if (rl.prm != nullptr) rl.ends[at] = make_uint4(rr.y, rr.z, (uint32_t)it_, (uint32_t)ir_);
+        }
+        if (rl.prm != nullptr && lane < Q) rl.prm[(int64_t)lane * rl.stride + at] = mine_q;
+      }
+    }
+  }
 }
 
 // One thread per listed candidate: up to refine_steps mixed steps (residual
@@ -1406,6 +1601,33 @@ static int grid_for(mpt_ctx* ctx, K kernel, const mpt_schedule* sch, size_t smem
   return ctx->sms * occ;
 }
 
+// The solver of order N: one candidate per lane (k_gn), or one per warp
+// (k_gn_warp) for the orders the schedule's warp_orders names (FP32
+// precisions only).
+template <int N, int PREC>
+static void launch_gn(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, const float4* ends32, const CandView& cv,
+                      const SolView& sv, const SolveCfg& cfg, const mpt_schedule* sch, RefineList rl, bool curved,
+                      cudaStream_t s) {
+  unsigned long long* counter = ctx->counters + (N - 1);
+  if constexpr (PREC != MPT_FP64_PLAIN) {
+    if (sch != nullptr && ((sch->warp_orders >> (N - 1)) & 1) != 0) {
+      if (curved)
+        k_gn_warp<N, PREC, true><<<grid_for(ctx, k_gn_warp<N, PREC, true>, sch), SOLVE_BLOCK, 0, s>>>(
+            sc, ep, ends32, cv, sv, cfg, counter, rl);
+      else
+        k_gn_warp<N, PREC, false><<<grid_for(ctx, k_gn_warp<N, PREC, false>, sch), SOLVE_BLOCK, 0, s>>>(
+            sc, ep, ends32, cv, sv, cfg, counter, rl);
+      return;
+    }
+  }
+  if (curved)
+    k_gn<N, PREC, true><<<grid_for(ctx, k_gn<N, PREC, true>, sch), SOLVE_BLOCK, 0, s>>>(sc, ep, ends32, cv, sv, cfg,
+                                                                                       counter, rl);
+  else
+    k_gn<N, PREC, false><<<grid_for(ctx, k_gn<N, PREC, false>, sch), SOLVE_BLOCK, 0, s>>>(sc, ep, ends32, cv, sv,
+                                                                                         cfg, counter, rl);
+}
+
 template <int PREC>
 static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, const float4* ends32, const CandView& cv,
                        const SolView& sv, const SolveCfg& cfg, const mpt_schedule* sch, RefineList rl,
@@ -1434,12 +1656,7 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
   {                                                                                                            \
     cudaStream_t s_ = (S);                                                                                     \
     if (per_order) {                                                                                           \
-      if (curved)                                                                                              \
-        k_gn<N, PREC, true><<<grid_for(ctx, k_gn<N, PREC, true>, sch), SOLVE_BLOCK, 0, s_>>>(                  \
-            sc, ep, ends32, cv, sv, cfg, ctx->counters + (N - 1), rl);                                         \
-      else                                                                                                     \
-        k_gn<N, PREC, false><<<grid_for(ctx, k_gn<N, PREC, false>, sch), SOLVE_BLOCK, 0, s_>>>(                \
-            sc, ep, ends32, cv, sv, cfg, ctx->counters + (N - 1), rl);                                         \
+      launch_gn<N, PREC>(ctx, sc, ep, ends32, cv, sv, cfg, sch, rl, curved, s_);                                \
       MPT_LAUNCH_CHECK();                                                                                      \
     }                                                                                                          \
     if (PREC == MPT_FP32_FP64REFINE) {                                                                         \

@@ -7,6 +7,8 @@
 //   blocks_per_sm  resident blocks of the persistent solver grids
 //   mixed_orders   one persistent launch over every order, or one per order
 //   prescreen      visibility prescreen before the refinement (on / off)
+//   warp_orders    orders whose FP32 iterations run one candidate per warp
+//                  (none, 4, 3-4, all) instead of one per lane
 // (the iteration cap is part of the method's stopping rule and is not tuned).
 // The search is a coordinate descent from the library defaults, two sweeps,
 // each trial timed with CUDA events as the best of two solves after a
@@ -97,6 +99,7 @@ int autotune(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, co
       {&mpt_schedule::blocks_per_sm, {0, 4, 3, 2}, 4},
       {&mpt_schedule::mixed_orders, {0, 1}, 2},
       {&mpt_schedule::prescreen, {1, 2}, precision == MPT_FP32_FP64REFINE ? 2 : 0},
+      {&mpt_schedule::warp_orders, {0, 8, 12, 15}, precision == MPT_FP64_PLAIN ? 0 : 4},
   };
   for (int sweep = 0; sweep < 2 && rc == MPT_OK; ++sweep) {
     bool moved = false;

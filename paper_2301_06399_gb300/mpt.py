@@ -54,7 +54,7 @@ class SolStruct(C.Structure):
 class Schedule(C.Structure):
     _fields_ = [("block", I32), ("blocks_per_sm", I32), ("tile", I32), ("max_iters", I32),
                 ("refine_steps", I32), ("mixed_orders", I32), ("refill_min", I32), ("prescreen", I32),
-                ("fallback", I32)]
+                ("fallback", I32), ("warp_orders", I32)]
 
 
 class PathStruct(C.Structure):
@@ -336,9 +336,9 @@ def alloc_solutions(capacity: int, device, keep_fp32: bool = False) -> Solutions
 
 
 def schedule_struct(block=128, blocks_per_sm=0, tile=0, max_iters=0, refine_steps=0, mixed_orders=0,
-                    refill_min=0, prescreen=0, fallback=0) -> Schedule:
+                    refill_min=0, prescreen=0, fallback=0, warp_orders=0) -> Schedule:
     return Schedule(block, blocks_per_sm, tile, max_iters, refine_steps, mixed_orders, refill_min, prescreen,
-                    fallback)
+                    fallback, warp_orders)
 
 
 def solve(ds: DeviceScene, cands: Candidates, precision: int = FP32_FP64REFINE, schedule: Schedule | None = None,

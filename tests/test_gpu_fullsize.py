@@ -65,25 +65,31 @@ def test_urban_block_every_candidate(mpt, ctx):
     _check_full_set(mpt, ctx, sc, S.CONFIG_SPECS["urban_block"], 2, "urban_block_32x32rx_order2")
 
 
-@pytest.mark.parametrize("mixed", [0, 1])
-def test_mixed_orders_every_candidate(mpt, ctx, mixed):
+SCHEDULES = {"per_order": {}, "single_launch": {"mixed_orders": 1}, "warp_per_path": {"warp_orders": 15}}
+
+
+@pytest.mark.parametrize("sched", list(SCHEDULES))
+def test_mixed_orders_every_candidate(mpt, ctx, sched):
     """Orders 1-4 mixed (2,097,152 candidates, consecutive edge diffractions
-    included), per-order launches and the single persistent launch over
-    every order, each compared with the oracle candidate by candidate."""
+    included) under three schedules: per-order launches, the single
+    persistent launch over every order, and one candidate per warp for every
+    order; each compared with the oracle candidate by candidate."""
     sc = S.mixed_order_city()
-    sched = mpt.schedule_struct(mixed_orders=mixed)
-    _check_full_set(mpt, ctx, sc, S.CONFIG_SPECS["mixed_order"], 4,
-                    f"mixed_orders_{'single_launch' if mixed else 'per_order'}", sched)
+    _check_full_set(mpt, ctx, sc, S.CONFIG_SPECS["mixed_order"], 4, f"mixed_orders_{sched}",
+                    mpt.schedule_struct(**SCHEDULES[sched]))
 
 
-def test_curved_root_sets_at_full_size(mpt, ctx):
+@pytest.mark.parametrize("warp_orders", [0, 7])
+def test_curved_root_sets_at_full_size(mpt, ctx, warp_orders):
     """Paraboloids, arcs and posed rectangles, 4,096 TX/RX pairs, orders 1-3,
     8 starts for curved sequences: for every (pair, sequence) the sets of
-    distinct valid roots of the GPU and of the oracle are identical."""
+    distinct valid roots of the GPU and of the oracle are identical; with
+    one candidate per lane (the default) and one per warp for every order."""
     sc = S.curved_scene(n_pairs=4096)
     spec = S.CONFIG_SPECS["curved"]
     ds = mpt.DeviceScene(ctx, sc)
-    cands, sols, paths = _trace(mpt, ds, 3, spec, mpt.FP32_FP64REFINE)
+    cands, sols, paths = _trace(mpt, ds, 3, spec, mpt.FP32_FP64REFINE,
+                                mpt.schedule_struct(warp_orders=warp_orders) if warp_orders else None)
     table = oracle.enumerate_sequences(sc, 3, spec)
     gpu = F.gpu_side(paths, sols)
     rep = F.compare_workload(sc, table, gpu, keep_sets=True)
@@ -93,7 +99,8 @@ def test_curved_root_sets_at_full_size(mpt, ctx):
     keep = np.isin(rep.valid_idx, same)
     sub = F.Report(valid_idx=rep.valid_idx[keep], valid_X=rep.valid_X[keep])
     err32 = F.fp32_point_error(sc, table, sub, sols.T32.cpu().numpy())
-    print(f"\nPER-CONFIG curved_4096pairs_order3: {rep.summary()}; root-set groups {n_groups}, differing "
+    print(f"\nPER-CONFIG curved_4096pairs_order3{'_warp_per_path' if warp_orders else ''}: {rep.summary()}; "
+          f"root-set groups {n_groups}, differing "
           f"{len(diffs)}; FP32-only max point error {err32:.2e} m")
     for d in diffs[:20]:
         print("  root-set difference:", d)
