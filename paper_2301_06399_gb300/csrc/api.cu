@@ -359,7 +359,9 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
     }
   }
   const size_t s_gb = align256((size_t)ng * 32 + 16);
-  const size_t total = s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb + s_a32 + s_gb + s_aff + s_own;
+  const size_t s_side = no <= mpt::SIDE_MAX_OBJ ? align256((size_t)no * no) : 0;
+  const size_t total =
+      s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb + s_a32 + s_gb + s_aff + s_own + s_side;
   MPT_CUDA_TRY(cudaSetDevice(ctx->device));
   void* mem = nullptr;
   MPT_CUDA_TRY(cudaMalloc(&mem, total));
@@ -396,10 +398,13 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   d.gbox = reinterpret_cast<const float4*>(put(gbox.data(), (size_t)ng * 32, s_gb));
   d.aff = reinterpret_cast<const float4*>(put(aff.data(), (size_t)no * 128, s_aff));
   d.own_occ = reinterpret_cast<const int32_t*>(put(own_occ.data(), (size_t)no * 4, s_own));
+  d.side = s_side ? reinterpret_cast<const int8_t*>(put(nullptr, 0, s_side)) : nullptr;  // built on the device
   d.scale = desc->scale;
   s->signature = fnv1a(image.data(), total, fnv1a(&desc->scale, sizeof(double)));
   s->alloc_bytes = total;
   cudaError_t e = cudaMemcpy(mem, image.data(), total, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && launch_side_table(d, nullptr) != MPT_OK) e = cudaErrorLaunchFailure;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     cudaFree(mem);

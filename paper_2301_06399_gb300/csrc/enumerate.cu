@@ -408,6 +408,40 @@ __global__ void k_visibility(DevScene sc, double delta, uint8_t* V) {
   }
 }
 
+// side[i][j] for plane i: +1 when every vertex of object j lies more than
+// delta in front of plane i (<n, X - O> > delta), -1 when every vertex lies
+// more than delta behind it, else 0; 0 for non-planes i.
+__global__ void k_side_table(DevScene sc, double delta, int8_t* side) {
+  const int64_t n = sc.n_obj;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / n), j = (int)(q % n);
+    int8_t v = 0;
+    if (i != j && sc.kind[i] == K_PLANE) {
+      const Rec<double> p = load_obj64(sc, i);
+      const v3<double> O = p.f3(0), nrm = p.f3(12);
+      v3<double> x[8];
+      const int m = object_vertices(sc, j, x);
+      bool front = true, behind = true;
+      for (int k = 0; k < m; ++k) {
+        const double h = dot(nrm, x[k] - O);
+        front = front && h > delta;
+        behind = behind && h < -delta;
+      }
+      v = front ? (int8_t)1 : behind ? (int8_t)-1 : (int8_t)0;
+    }
+    side[q] = v;
+  }
+}
+
+int launch_side_table(const DevScene& d, cudaStream_t st) {
+  if (d.side == nullptr) return MPT_OK;
+  const int64_t pairs = (int64_t)d.n_obj * d.n_obj;
+  const int64_t blocks = (pairs + 255) / 256 < 1024 ? (pairs + 255) / 256 : 1024;
+  k_side_table<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(d, 1e-6 * d.scale, const_cast<int8_t*>(d.side));
+  MPT_LAUNCH_CHECK();
+  return MPT_OK;
+}
+
 int launch_visibility(mpt_ctx* ctx, const mpt_scene* scene, uint8_t* vis, cudaStream_t st) {
   const int64_t pairs = (int64_t)scene->d.n_obj * scene->d.n_obj;
   int64_t blocks = (pairs + 255) / 256;

@@ -31,6 +31,8 @@ struct DevScene {
   const float4* gbox;       // [2][n_grp]: boxes of groups of OCC_GROUP consecutive occluders
   const float4* aff;        // [n_obj][8]: float-float records (head, tail) x 16, object-major
   const int32_t* own_occ;   // [n_obj]: the occluder rectangle that is a plane's own facet, or -1
+  const int8_t* side;       // [n_obj][n_obj] or null: side[i*n_obj + j] = +1 (-1) when object j lies wholly
+                            // more than 1e-6 S in front of (behind) plane i, else 0 (0 for non-planes i)
   double scale;
 };
 
@@ -276,6 +278,9 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
 int launch_enumerate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, int max_order,
                      const uint8_t* adj, const mpt_sampling* smp, mpt_candidates* out, cudaStream_t st);
 int launch_visibility(mpt_ctx* ctx, const mpt_scene* scene, uint8_t* vis, cudaStream_t st);
+// Object-side table of a scene (DevScene::side), rebuilt whenever planes move.
+constexpr int SIDE_MAX_OBJ = 4096;
+int launch_side_table(const DevScene& d, cudaStream_t st);
 int launch_image(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,
                  mpt_solutions* out, cudaStream_t st);
 void tune_cache_free(mpt_ctx* ctx);

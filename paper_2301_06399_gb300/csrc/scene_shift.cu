@@ -110,7 +110,7 @@ int launch_shift_planes(mpt_ctx* ctx, const mpt_scene* base, mpt_scene* dst, con
     k_group_boxes<<<(dst->d.n_grp + SHIFT_BLOCK - 1) / SHIFT_BLOCK, SHIFT_BLOCK, 0, st>>>(dst->d);
     MPT_LAUNCH_CHECK();
   }
-  return MPT_OK;
+  return launch_side_table(dst->d, st);  // the planes moved
 }
 
 }  // namespace mpt

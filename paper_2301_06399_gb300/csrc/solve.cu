@@ -43,6 +43,7 @@ struct SolveCfg {
   float mu32;
   double mu64;
   int prescreen;     // 1: visibility prescreen before the refinement
+  int exclude;       // 1: half-space exclusion before iterating
   int fallback;  // k_refine_fb mode: FB_FF, FB_F64 or FB_F64_WARP
 };
 
@@ -263,6 +264,68 @@ __device__ __forceinline__ Rec<R> load_obj_kind(const DevScene& s, int o) {
     return load_obj64(s, o);
 }
 
+// ------------------------------------------------------- exclusion test --
+// The half-space condition of Eq. 8: a reflection sends the outgoing segment
+// back to the side of its plane that the incoming one came from, so the two
+// neighbouring points of a reflection lie on one side of its plane.  A
+// candidate whose reflection has TX (first interaction), RX (last) or a
+// neighbouring object wholly on the side opposite to its other neighbour
+// has no path (its cost cannot fall below ~1e-11) and is excluded before
+// iterating.  Margins: an endpoint more than 1e-5 S off the plane (far above
+// the rounding of its FP32 distance), an object wholly more than 1e-6 S off
+// it (the FP64 side table).
+template <class R>
+__device__ __forceinline__ R plane_dist(const DevScene& s, int o, const v3<R>& X) {
+  if constexpr (std::is_same<R, float>::value) {
+    const float4 q0 = __ldg(s.a32 + 4 * o), q3 = __ldg(s.a32 + 4 * o + 3);
+    return dot(mk(q3.x, q3.y, q3.z), X - mk(q0.x, q0.y, q0.z));
+  } else {
+    const double2 a = __ldg(&s.o64[o]), b = __ldg(&s.o64[s.n_obj + o]);
+    const double2 c = __ldg(&s.o64[6 * s.n_obj + o]), d = __ldg(&s.o64[7 * s.n_obj + o]);
+    return dot(mk(c.x, c.y, d.x), X - mk(a.x, a.y, b.x));
+  }
+}
+
+template <int N, class R>
+__device__ __forceinline__ bool excluded(const DevScene& sc, const DevEnds& ep, const float4* ends32,
+                                         const int (&id)[N], const int (&kind)[N], int it_, int ir_,
+                                         bool exclude) {
+  if (sc.side == nullptr || !exclude) return false;
+  const R m = R(1e-5 * sc.scale);
+  const int n = sc.n_obj;
+  bool ex = false;
+  if (kind[0] == K_PLANE) {
+    const R a = plane_dist<R>(sc, id[0], load_end<R>(ep.tx, ends32, it_));
+    if (N == 1) {
+      const R b = plane_dist<R>(sc, id[0], load_end<R>(ep.rx, ends32 + ep.n_tx, ir_));
+      ex = (a > m && b < -m) || (a < -m && b > m);
+    } else {
+      const int cls = __ldg(sc.side + (int64_t)id[0] * n + id[N > 1 ? 1 : 0]);
+      ex = (a > m && cls < 0) || (a < -m && cls > 0);
+    }
+  }
+  if (N >= 2 && kind[N - 1] == K_PLANE) {
+    const R b = plane_dist<R>(sc, id[N - 1], load_end<R>(ep.rx, ends32 + ep.n_tx, ir_));
+    const int cls = __ldg(sc.side + (int64_t)id[N - 1] * n + id[N >= 2 ? N - 2 : 0]);
+    ex = ex || (b > m && cls < 0) || (b < -m && cls > 0);
+  }
+#pragma unroll
+  for (int k = 1; k + 1 < N; ++k)
+    if (kind[k] == K_PLANE) {
+      const int c0 = __ldg(sc.side + (int64_t)id[k] * n + id[k - 1]);
+      const int c1 = __ldg(sc.side + (int64_t)id[k] * n + id[k + 1]);
+      ex = ex || c0 * c1 < 0;
+    }
+  return ex;
+}
+
+__device__ __forceinline__ void write_excluded(const SolView& out, int64_t c) {
+  out.cost[c] = (double)INFINITY;
+  out.status[c] = (uint8_t)MPT_PATH_EXCLUDED;
+  out.iters[c] = 0;
+  out.evals[c] = 0;
+}
+
 // ------------------------------------------------------------- kernel A --
 // The lanes of one warp solve the candidates of order N in [begin, end).
 // With a counter, the warp claims pieces of the range as it goes (work
@@ -456,17 +519,30 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
         const int slot = cur_pos + rank;
         cur_pos += nneed < avail ? nneed : avail;
         if (take) {
-          need = false;
           const int64_t idx = cur_base + slot;
           const uint4 rr = rbuf[buf][slot];
           // a record of this solver's order whose objects and endpoints exist
           bool valid = (int)(rr.w & 0xFFu) == N;
+          int id[N], kd[N];
 #pragma unroll
-          for (int k = 0; k < N; ++k)
-            valid = valid && (int)(((k < 2 ? rr.y : rr.z) >> (16 * (k & 1))) & 0xFFFFu) < sc.n_obj;
-          pair_ends(ep, rr.x, it_, ir_);
-          valid = valid && it_ < ep.n_tx && ir_ < ep.n_rx;
+          for (int k = 0; k < N; ++k) {
+            id[k] = (int)(((k < 2 ? rr.y : rr.z) >> (16 * (k & 1))) & 0xFFFFu);
+            valid = valid && id[k] < sc.n_obj;
+          }
+          int t_, r_;
+          pair_ends(ep, rr.x, t_, r_);
+          valid = valid && t_ < ep.n_tx && r_ < ep.n_rx;
           if (valid) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) kd[k] = __ldg(sc.kind + id[k]);
+          }
+          if (valid && excluded<N, R>(sc, ep, ends32, id, kd, t_, r_, cfg.exclude)) {
+            // no path: written now; the lane takes another candidate
+            write_excluded(out, idx);
+          } else if (valid) {
+            need = false;
+            it_ = t_;
+            ir_ = r_;
             // only the record is decoded here; the initial guess is made in
             // the first pass, from the records and endpoints it loads anyway
             c = (int)(idx - begin);
@@ -479,10 +555,9 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
             lm_ratio = R(cfg.localmin_ratio_planar);
 #pragma unroll
             for (int k = 0; k < N; ++k) {
-              const int kd = __ldg(sc.kind + (int)(((k < 2 ? rr.y : rr.z) >> (16 * (k & 1))) & 0xFFFFu));
-              kinds |= kd << (8 * k);
-              pat |= (kd == K_LINE ? 1 : 0) << k;
-              if (CURVED && (kd == K_PARAB || kd == K_ARC)) lm_ratio = R(cfg.localmin_ratio);
+              kinds |= kd[k] << (8 * k);
+              pat |= (kd[k] == K_LINE ? 1 : 0) << k;
+              if (CURVED && (kd[k] == K_PARAB || kd[k] == K_ARC)) lm_ratio = R(cfg.localmin_ratio);
             }
             fresh = true;
             iters = 0;
@@ -1282,6 +1357,10 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_warp(DevScene sc, DevEnds ep
         kind[k] = __ldg(sc.kind + ids[k]);
         if (CURVED && (kind[k] == K_PARAB || kind[k] == K_ARC)) lm_ratio = cfg.localmin_ratio;
       }
+      if (excluded<N, float>(sc, ep, ends32, ids, kind, it_, ir_, cfg.exclude)) {
+        if (lane == 0) write_excluded(out, c);
+        continue;
+      }
       // this lane's object (point lane / 2); lanes past the sequence hold zeros
       Rec<float> rm;
 #pragma unroll
@@ -1708,6 +1787,7 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
   cfg.piece = (sch && sch->tile > 0) ? (sch->tile < 32 ? 32 : (sch->tile > GN_CHUNK ? GN_CHUNK : sch->tile)) : GN_CHUNK;
   cfg.fallback_iters = 2;  // at most 5 evaluations
   cfg.prescreen = (sch && sch->prescreen == 2) ? 0 : 1;
+  cfg.exclude = (sch && sch->exclude == 2) ? 0 : 1;
   cfg.fallback = !sch ? FB_F64_WARP : sch->fallback == 1 ? FB_FF : sch->fallback == 3 ? FB_F64 : FB_F64_WARP;
   const double S = scene->d.scale;
   cfg.c_tol32 = 1e-12f;

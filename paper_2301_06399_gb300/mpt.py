@@ -21,7 +21,7 @@ P, I32, I64, U64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
 
 MPT_OK, MPT_ERR_ARG, MPT_ERR_CUDA, MPT_ERR_CAPACITY, MPT_ERR_TIMEOUT, MPT_ERR_UNSUPPORTED = range(6)
 FP64_PLAIN, FP32, FP32_FP64REFINE = 0, 1, 2
-PATH_CONVERGED, PATH_MAXITER, PATH_DIVERGED, PATH_STALLED, PATH_NONFINITE = range(5)
+PATH_CONVERGED, PATH_MAXITER, PATH_DIVERGED, PATH_STALLED, PATH_NONFINITE, PATH_EXCLUDED = range(6)
 PATH_REFINED, PATH_PRESCREENED, PATH_FALLBACK = 0x10, 0x20, 0x40
 TAU = 1e-20  # acceptance threshold on the cost of Eq. 15
 
@@ -54,7 +54,8 @@ class SolStruct(C.Structure):
 class Schedule(C.Structure):
     _fields_ = [("block", I32), ("blocks_per_sm", I32), ("tile", I32), ("max_iters", I32),
                 ("refine_steps", I32), ("mixed_orders", I32), ("refill_min", I32), ("prescreen", I32),
-                ("fallback", I32), ("warp_orders", I32)]
+                ("fallback", I32), ("warp_orders", I32),
+                ("exclude", I32)]
 
 
 class PathStruct(C.Structure):
@@ -336,9 +337,9 @@ def alloc_solutions(capacity: int, device, keep_fp32: bool = False) -> Solutions
 
 
 def schedule_struct(block=128, blocks_per_sm=0, tile=0, max_iters=0, refine_steps=0, mixed_orders=0,
-                    refill_min=0, prescreen=0, fallback=0, warp_orders=0) -> Schedule:
+                    refill_min=0, prescreen=0, fallback=0, warp_orders=0, exclude=0) -> Schedule:
     return Schedule(block, blocks_per_sm, tile, max_iters, refine_steps, mixed_orders, refill_min, prescreen,
-                    fallback, warp_orders)
+                    fallback, warp_orders, exclude)
 
 
 def solve(ds: DeviceScene, cands: Candidates, precision: int = FP32_FP64REFINE, schedule: Schedule | None = None,

@@ -239,3 +239,60 @@ def fp32_point_error(sc, table, rep: Report, T32: np.ndarray):
     order = table.order[c // sc.n_pairs]
     col = np.arange(12)[None, :] < 3 * order[:, None]
     return float(np.where(col, np.abs(X32 - rep.valid_X), 0.0).max())
+
+
+def exclusion_mask(sc, table, m_tx: float = 1e-5, m_obj: float = 1e-6) -> np.ndarray:
+    """Candidates (c = entry * n_pairs + pair) whose reflection on a plane has
+    its two neighbouring points certainly on opposite sides of the plane: the
+    first reflection with TX more than m_tx * S on one side and the next
+    object wholly (every vertex of oracle._object_vertices) more than
+    m_obj * S on the other side (RX for a single reflection), the last
+    reflection likewise with RX and the previous object, an inner reflection
+    with its two neighbouring objects on opposite sides.  Eq. 8 makes the
+    outgoing direction r = i - 2 <i, n> n leave on the side the incoming
+    direction came from, so none of these candidates has a path.  Written
+    from that condition with numpy, independently of the solver's code."""
+    kinds = np.asarray(sc.obj_kind)
+    par = np.asarray(sc.obj_param, np.float64)
+    n = len(kinds)
+    verts = [np.asarray(oracle._object_vertices(int(kinds[i]), par[i])) for i in range(n)]
+    tx, rx = np.asarray(sc.tx, np.float64), np.asarray(sc.rx, np.float64)
+    if sc.pair_mode == 0:
+        A, B = np.repeat(tx, len(rx), axis=0), np.tile(rx, (len(tx), 1))
+    else:
+        A, B = tx, rx
+    mt, mo = m_tx * sc.scale, m_obj * sc.scale
+
+    def dist(i, X):  # signed distance to plane i: <n, X - O>
+        return (X - par[i][4:7]) @ par[i][0:3]
+
+    side = np.zeros((n, n), np.int8)  # +1 / -1: object j wholly in front of / behind plane i
+    for i in range(n):
+        if kinds[i] != 0:
+            continue
+        for j in range(n):
+            if j != i:
+                d = dist(i, verts[j])
+                side[i, j] = 1 if d.min() > mo else (-1 if d.max() < -mo else 0)
+    out = np.zeros(len(table) * len(A), bool)
+    for e in range(len(table)):
+        o = int(table.order[e])
+        ids = [int(x) for x in table.ids[e][:o]]
+        ex = np.zeros(len(A), bool)
+        if kinds[ids[0]] == 0:
+            a = dist(ids[0], A)
+            if o == 1:
+                b = dist(ids[0], B)
+                ex |= ((a > mt) & (b < -mt)) | ((a < -mt) & (b > mt))
+            else:
+                s = side[ids[0], ids[1]]
+                ex |= ((a > mt) & (s < 0)) | ((a < -mt) & (s > 0))
+        if o >= 2 and kinds[ids[-1]] == 0:
+            b = dist(ids[-1], B)
+            s = side[ids[-1], ids[-2]]
+            ex |= ((b > mt) & (s < 0)) | ((b < -mt) & (s > 0))
+        for k in range(1, o - 1):
+            if kinds[ids[k]] == 0 and int(side[ids[k], ids[k - 1]]) * int(side[ids[k], ids[k + 1]]) < 0:
+                ex[:] = True
+        out[e * len(A):(e + 1) * len(A)] = ex
+    return out

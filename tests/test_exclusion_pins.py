@@ -1,0 +1,91 @@
+"""The solver's exclusion of candidates by the half-space condition of Eq. 8
+removes no path.
+
+Eq. 8 makes the outgoing direction of a reflection r = i - 2 <i, n> n, so
+<r, n> = -<i, n>: the segment after a reflection leaves on the side of the
+plane that the segment before it came from.  The solver therefore skips a
+candidate whose reflection has its two neighbouring points certainly on
+opposite sides of the plane (TX or RX more than 1e-5 S from the plane, a
+neighbouring object wholly more than 1e-6 S from it): with every point
+inside its object's bounds, the cost cannot fall below (1e-5 S / L)^2 ~
+1e-11 for path legs L of a few hundred metres.  The oracle does not use the
+condition, so it checks it: on reduced versions of the workloads, no
+candidate the oracle accepts is excluded, the excluded candidates that the
+oracle drives to a zero cost (on the unbounded planes and lines of the
+parametrisation) have a point outside its object's bounds, and the exclusion
+is not empty.
+"""
+import numpy as np
+import pytest
+
+import fullset as F
+import oracle
+from paper_2301_06399_gb300 import scenes as S
+
+
+def _reduced(name):
+    if name == "urban_block_8x8rx":
+        return S.urban_block(8), S.CONFIG_SPECS["urban_block"], 2
+    if name == "mixed_orders_1tx_64rx":
+        sc = S.mixed_order_city()
+        sc.tx = sc.tx[:1].copy()
+        sc.rx = np.ascontiguousarray(sc.rx[::4])
+        return sc.contiguous(), S.CONFIG_SPECS["mixed_order"], 4
+    return S.curved_scene(n_pairs=256), S.CONFIG_SPECS["curved"], 3
+
+
+def _outside(sc, i, s, t, tol=1e-6):
+    """Parameters (s, t) of object i outside its bounds by more than tol
+    (metres; parameters of planes, lines and paraboloids are lengths, an
+    arc's is an angle, taken over its radius)."""
+    p = np.asarray(sc.obj_param[i], np.float64)
+    kind = int(sc.obj_kind[i])
+    if kind == 0:
+        return s < -tol or s > p[13] + tol or t < -tol or t > p[14] + tol
+    if kind == 2:
+        return s < p[6] - tol or s > p[7] + tol
+    if kind == 1:
+        return np.hypot(s, t) > p[13] + tol
+    d = (s - p[10]) % (2.0 * np.pi)
+    return d > (p[11] - p[10]) + tol / p[6] and d < 2.0 * np.pi - tol / p[6]
+
+
+@pytest.mark.parametrize("name", ["urban_block_8x8rx", "mixed_orders_1tx_64rx", "curved_256pairs"])
+def test_excluded_candidates_have_no_path(name):
+    sc, spec, mo = _reduced(name)
+    table = oracle.enumerate_sequences(sc, mo, spec)
+    sol, ver = oracle.candidate_range(sc, table, 0, len(table) * sc.n_pairs)
+    ex = F.exclusion_mask(sc, table)
+    assert len(ex) == len(sol.cost)
+    valid = ver.valid > 0
+    print(f"{name}: {len(ex)} candidates, {int(ex.sum())} excluded, {int(valid.sum())} oracle-valid, "
+          f"{int((ex & (ver.ambiguous > 0)).sum())} excluded and ambiguous")
+    assert not np.any(ex & valid), np.nonzero(ex & valid)[0][:10]
+    # a zero cost is reached only on the unbounded surfaces, with a point
+    # outside its object's bounds (the condition holds for bounded objects)
+    zero = np.nonzero(ex & np.isfinite(sol.cost) & (sol.cost < 1e-12))[0]
+    for c in zero:
+        e = c // sc.n_pairs
+        ids = table.ids[e][:int(table.order[e])]
+        assert any(_outside(sc, int(i), sol.T[c, 2 * k], sol.T[c, 2 * k + 1]) for k, i in enumerate(ids)), c
+    print(f"  {len(zero)} excluded candidates reach a zero cost outside their objects' bounds")
+    assert ex.mean() > 0.05
+
+
+def test_single_reflection_across_a_plane_is_excluded_and_has_no_path():
+    """TX and RX on opposite sides of one plane: the only candidate is
+    excluded, and the oracle finds no path for it."""
+    sc = S.street_canyon()
+    sc.tx = np.array([[0.0, -5.0, 10.0]])
+    sc.rx = np.array([[0.0, 15.0, 1.5]])  # beyond the wall y = +10
+    sc = sc.contiguous()
+    spec = S.SequenceSpec(quota=(-1, 0, 0, 0))
+    table = oracle.enumerate_sequences(sc, 1, spec)
+    ex = F.exclusion_mask(sc, table)
+    sol, ver = oracle.candidate_range(sc, table, 0, len(table) * sc.n_pairs)
+    ids = [int(table.ids[e][0]) for e in range(len(table))]
+    # the wall y = +10 (normal along y, origin at y = 10) separates TX and RX
+    wall = [e for e, i in enumerate(ids) if abs(abs(sc.obj_param[i][1]) - 1.0) < 1e-12 and sc.obj_param[i][5] == 10.0]
+    assert len(wall) == 1
+    assert ex[wall[0]] and not ver.valid[wall[0]]
+    assert not np.isfinite(sol.cost[wall[0]]) or sol.cost[wall[0]] > 1e-6

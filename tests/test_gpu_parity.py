@@ -272,6 +272,37 @@ def test_mixed_orders_single_launch_matches_per_order(mpt, ctx):
     assert torch.allclose(p1.X[:, :p1.n()], p2.X[:, :p2.n()], atol=1e-9, rtol=0)
 
 
+@pytest.mark.parametrize("prec", ["FP32_FP64REFINE", "FP64_PLAIN"])
+@pytest.mark.parametrize("name", ["urban_block", "mixed_order", "curved"])
+def test_excluded_candidates_match_the_half_space_condition(mpt, ctx, name, prec):
+    """The solver's MPT_PATH_EXCLUDED candidates (half-space condition of
+    Eq. 8, tested before iterating) against the condition written with numpy
+    in FP64 (fullset.exclusion_mask): the GPU set lies between the masks with
+    the margins 10% wider and 10% narrower (the GPU tests endpoints in the
+    solver's precision), and is a quarter or so of the candidates."""
+    import fullset as F
+    if name == "urban_block":
+        sc, order = S.urban_block(32), 2
+    elif name == "mixed_order":
+        sc, order = S.mixed_order_city(), 4
+    else:
+        sc, order = S.curved_scene(), 3
+    if prec == "FP64_PLAIN" and name != "mixed_order":
+        pytest.skip("the plain FP64 method is checked on the mixed-order city")
+    spec = S.CONFIG_SPECS[name]
+    _, cands, sols, _ = gpu_trace(mpt, ctx, sc, order, spec, precision=getattr(mpt, prec), path_cap=1 << 21)
+    n = int(cands.count.item())
+    got = ((sols.status[:n] & 0x0F) == mpt.PATH_EXCLUDED).cpu().numpy()
+    table = oracle.enumerate_sequences(sc, order, spec)
+    wide = F.exclusion_mask(sc, table, m_tx=0.9e-5, m_obj=0.9e-6)
+    narrow = F.exclusion_mask(sc, table, m_tx=1.1e-5, m_obj=1.1e-6)
+    print(f"{name} {prec}: {int(got.sum())} of {n} excluded (numpy {int(narrow.sum())}..{int(wide.sum())})")
+    assert not np.any(narrow & ~got), np.nonzero(narrow & ~got)[0][:10]
+    assert not np.any(got & ~wide), np.nonzero(got & ~wide)[0][:10]
+    assert got.mean() > 0.05
+    assert np.all(np.isinf(sols.cost[:n].cpu().numpy()[got]))
+
+
 @pytest.mark.parametrize("name", ["urban_block", "curved"])
 def test_warp_fallback_equals_single_lane_fallback(mpt, ctx, name):
     """The refinement's fallback with its FP64 evaluation spread over a warp
