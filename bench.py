@@ -381,6 +381,7 @@ def run_ours(args):
             step()
         stream.synchronize()
         n_valid = paths.n()
+        n_excluded = int(((sols.status[:n_cand] & 0x0F) == mpt.PATH_EXCLUDED).sum().item())
         flops = algorithmic_flops(mpt, sc, cands, sols, n_cand)
         # enumerate (2) + solve (endpoint copy, solver launches, per order the
         # visibility prescreen if on, refinement and its fallback) + validate
@@ -641,6 +642,8 @@ def run_ours(args):
                    "parallelism": f"weak: one process per GPU, {ws} GPU(s)"},
         "valid_paths_per_step": n_valid,
         "valid_paths_per_sec": n_valid * ws / (ms_per_step * 1e-3),
+        "excluded_per_step": n_excluded,
+        "iterated_per_step": n_cand - n_excluded,
         "roofline": {"kernel": "mpt_solve (k_gn orders 1-4 + visibility prescreen + k_refine)", "bound": "alu",
                      "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {SM_MAX_MHZ_NOMINAL:.0f} MHz (derived)",

@@ -98,9 +98,8 @@ enum {
   MPT_PATH_DIVERGED = 2,    /* a point left the cube of half-side 1e3 S */
   MPT_PATH_STALLED = 3,     /* line search could not decrease the cost */
   MPT_PATH_NONFINITE = 4,   /* NaN / Inf in the cost */
-  MPT_PATH_EXCLUDED = 5,    /* no path by the half-space condition of Eq. 8 (a
-                               reflection's neighbouring points must lie on the
-                               same side of its plane): not iterated, cost +inf,
+  MPT_PATH_EXCLUDED = 5,    /* no path by the half-space or beam condition of
+                               Eq. 8 (see mpt_solve): not iterated, cost +inf,
                                parameters untouched, iters = evals = 0 */
   MPT_PATH_REFINED = 0x10,  /* flag: final stage ran (FP64 solve or refinement) */
   MPT_PATH_PRESCREENED = 0x20, /* flag: FP32 prescreen rejected (no refinement) */
@@ -206,8 +205,8 @@ typedef struct {
                              lanes (same minimiser and stopping rules); 0 (the
                              default): one candidate per lane for every order.
                              Applies to per-order launches (mixed_orders = 0) */
-  int32_t exclude;        /* half-space exclusion of candidates before iterating
-                             (see mpt_solve): 0 library default (on), 1 on, 2 off
+  int32_t exclude;        /* exclusion of candidates before iterating (see
+                             mpt_solve): 0 library default (on), 1 on, 2 off
                              (every candidate iterated; the same valid paths) */
 } mpt_schedule;
 
@@ -296,18 +295,27 @@ int64_t mpt_candidate_count(const mpt_scene* scene, const mpt_endpoints* ends, i
  * cand->capacity) candidates on the device.  precision: MPT_FP64_PLAIN,
  * MPT_FP32 or MPT_FP32_FP64REFINE.  out->capacity must be >= cand->capacity
  * and cand->capacity below 2^31 (MPT_ERR_CAPACITY otherwise).
- * Before iterating, a candidate is excluded (status MPT_PATH_EXCLUDED) when
- * a reflection on a plane has its two neighbouring points certainly on
- * opposite sides of that plane: the first reflection with TX more than
- * 1e-5 S on one side and the next object (or RX) wholly more than 1e-6 S on
- * the other (every vertex, as for mpt_visibility), the last likewise with
- * RX, an inner one with its two neighbouring objects.  Eq. 8 sends the
- * outgoing segment back to the side the incoming one came from, so with its
+ * Before iterating (per-order launches; mixed_orders = 1 iterates every
+ * candidate), one pass excludes (status MPT_PATH_EXCLUDED) the candidates
+ * that two consequences of Eq. 8 rule out.  The outgoing direction of a
+ * reflection is the direction from the mirror image of the previous point
+ * through the reflection point, so (half-space) the neighbouring points of a
+ * reflection lie on one side of its plane, and (beam) after the first
+ * reflection the next point lies in the pyramid from TX's mirror image
+ * through the reflecting rectangle, before the last one the previous point
+ * in the pyramid from RX's image.  Excluded: the first reflection with TX
+ * more than 1e-5 S on one side of its plane and the next object (or RX)
+ * wholly more than 1e-6 S on the other (every vertex, as for
+ * mpt_visibility); the next object (or RX) wholly more than 1e-5 S outside
+ * one face of the pyramid, TX being more than 1e-2 S from the plane; the
+ * same for the last reflection with RX and the previous object; an inner
+ * reflection with its two neighbouring objects on opposite sides.  With its
  * points inside their objects' bounds such a candidate's cost stays above
- * ~1e-11, far above any acceptance threshold: the exclusion removes no
- * path.  The object-side table is built at
- * mpt_scene_upload (scenes of at most 4096 objects; larger scenes iterate
- * every candidate). */
+ * ~1e-11, far above any acceptance threshold: the exclusion removes no path.
+ * The object-side and vertex tables are built at mpt_scene_upload (scenes of
+ * at most 4096 objects; larger scenes, or more than 65535 endpoints, iterate
+ * every candidate); the pass uses context scratch of 4 bytes per candidate
+ * and 80 bytes per (endpoint, object). */
 int mpt_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
               const mpt_candidates* cand, int precision, const mpt_schedule* schedule,
               mpt_solutions* out, void* stream);

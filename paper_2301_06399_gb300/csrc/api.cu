@@ -133,6 +133,8 @@ int mpt_ctx_create(int device, mpt_ctx** out) {
   c->rscratch_bytes = 0;
   c->escratch = nullptr;
   c->escratch_bytes = 0;
+  c->xscratch = nullptr;
+  c->xscratch_bytes = 0;
   c->tune_cache = nullptr;
   *out = c;
   return MPT_OK;
@@ -145,6 +147,7 @@ int mpt_ctx_destroy(mpt_ctx* ctx) {
   if (ctx->vscratch) cudaFree(ctx->vscratch);
   if (ctx->rscratch) cudaFree(ctx->rscratch);
   if (ctx->escratch) cudaFree(ctx->escratch);
+  if (ctx->xscratch) cudaFree(ctx->xscratch);
   cudaFree(ctx->counters);
   for (int i = 0; i < 3; ++i) {
     cudaStreamDestroy(ctx->aux[i]);
@@ -360,8 +363,9 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   }
   const size_t s_gb = align256((size_t)ng * 32 + 16);
   const size_t s_side = no <= mpt::SIDE_MAX_OBJ ? align256((size_t)no * no) : 0;
+  const size_t s_vtx = align256((size_t)no * 128);
   const size_t total =
-      s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb + s_a32 + s_gb + s_aff + s_own + s_side;
+      s_kind + s_o32 + s_o64 + s_ck + s_c32 + s_c64 + s_oo + s_cb + s_a32 + s_gb + s_aff + s_own + s_side + s_vtx;
   MPT_CUDA_TRY(cudaSetDevice(ctx->device));
   void* mem = nullptr;
   MPT_CUDA_TRY(cudaMalloc(&mem, total));
@@ -399,6 +403,7 @@ int mpt_scene_upload(mpt_ctx* ctx, const mpt_scene_desc* desc, mpt_scene** out) 
   d.aff = reinterpret_cast<const float4*>(put(aff.data(), (size_t)no * 128, s_aff));
   d.own_occ = reinterpret_cast<const int32_t*>(put(own_occ.data(), (size_t)no * 4, s_own));
   d.side = s_side ? reinterpret_cast<const int8_t*>(put(nullptr, 0, s_side)) : nullptr;  // built on the device
+  d.vtx = reinterpret_cast<const float4*>(put(nullptr, 0, s_vtx));                         // likewise
   d.scale = desc->scale;
   s->signature = fnv1a(image.data(), total, fnv1a(&desc->scale, sizeof(double)));
   s->alloc_bytes = total;

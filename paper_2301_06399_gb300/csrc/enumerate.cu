@@ -433,7 +433,24 @@ __global__ void k_side_table(DevScene sc, double delta, int8_t* side) {
   }
 }
 
+// vtx[o][k]: the points of object_vertices in FP32, the last one repeated
+// up to 8 (a repeated point changes no test over all of them).
+__global__ void k_vertices(DevScene sc, float4* vtx) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= sc.n_obj) return;
+  v3<double> x[8];
+  const int m = object_vertices(sc, o, x);
+  for (int k = 0; k < 8; ++k) {
+    const v3<double>& p = x[k < m ? k : m - 1];
+    vtx[(int64_t)o * 8 + k] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.f);
+  }
+}
+
 int launch_side_table(const DevScene& d, cudaStream_t st) {
+  if (d.vtx != nullptr) {
+    k_vertices<<<(d.n_obj + 127) / 128, 128, 0, st>>>(d, const_cast<float4*>(d.vtx));
+    MPT_LAUNCH_CHECK();
+  }
   if (d.side == nullptr) return MPT_OK;
   const int64_t pairs = (int64_t)d.n_obj * d.n_obj;
   const int64_t blocks = (pairs + 255) / 256 < 1024 ? (pairs + 255) / 256 : 1024;

@@ -33,6 +33,8 @@ struct DevScene {
   const int32_t* own_occ;   // [n_obj]: the occluder rectangle that is a plane's own facet, or -1
   const int8_t* side;       // [n_obj][n_obj] or null: side[i*n_obj + j] = +1 (-1) when object j lies wholly
                             // more than 1e-6 S in front of (behind) plane i, else 0 (0 for non-planes i)
+  const float4* vtx;        // [n_obj][8] or null: FP32 points whose convex hull holds the object (rectangle
+                            // corners, edge ends, paraboloid box corners, arc square corners; the last repeated)
   double scale;
 };
 
@@ -189,6 +191,10 @@ struct mpt_ctx {
   // FP32 endpoint copies, grown on demand
   void* escratch;
   size_t escratch_bytes;
+  // candidate exclusion: per-order lists of the iterated candidates and the
+  // reflection beams of every endpoint through every plane, grown on demand
+  void* xscratch;
+  size_t xscratch_bytes;
   // auxiliary streams for independent per-order chains, and the events that
   // fork them from and join them back to the caller's stream
   cudaStream_t aux[3];
@@ -278,7 +284,8 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
 int launch_enumerate(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, int max_order,
                      const uint8_t* adj, const mpt_sampling* smp, mpt_candidates* out, cudaStream_t st);
 int launch_visibility(mpt_ctx* ctx, const mpt_scene* scene, uint8_t* vis, cudaStream_t st);
-// Object-side table of a scene (DevScene::side), rebuilt whenever planes move.
+// Object-side table and vertex table of a scene (DevScene::side, ::vtx),
+// rebuilt whenever planes move.
 constexpr int SIDE_MAX_OBJ = 4096;
 int launch_side_table(const DevScene& d, cudaStream_t st);
 int launch_image(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends, const mpt_candidates* cand,

@@ -264,59 +264,128 @@ __device__ __forceinline__ Rec<R> load_obj_kind(const DevScene& s, int o) {
     return load_obj64(s, o);
 }
 
-// ------------------------------------------------------- exclusion test --
-// The half-space condition of Eq. 8: a reflection sends the outgoing segment
-// back to the side of its plane that the incoming one came from, so the two
-// neighbouring points of a reflection lie on one side of its plane.  A
-// candidate whose reflection has TX (first interaction), RX (last) or a
-// neighbouring object wholly on the side opposite to its other neighbour
-// has no path (its cost cannot fall below ~1e-11) and is excluded before
-// iterating.  Margins: an endpoint more than 1e-5 S off the plane (far above
-// the rounding of its FP32 distance), an object wholly more than 1e-6 S off
-// it (the FP64 side table).
-template <class R>
-__device__ __forceinline__ R plane_dist(const DevScene& s, int o, const v3<R>& X) {
-  if constexpr (std::is_same<R, float>::value) {
-    const float4 q0 = __ldg(s.a32 + 4 * o), q3 = __ldg(s.a32 + 4 * o + 3);
-    return dot(mk(q3.x, q3.y, q3.z), X - mk(q0.x, q0.y, q0.z));
-  } else {
-    const double2 a = __ldg(&s.o64[o]), b = __ldg(&s.o64[s.n_obj + o]);
-    const double2 c = __ldg(&s.o64[6 * s.n_obj + o]), d = __ldg(&s.o64[7 * s.n_obj + o]);
-    return dot(mk(c.x, c.y, d.x), X - mk(a.x, a.y, b.x));
-  }
+// ------------------------------------------------------- exclusion pass --
+// Two necessary conditions of Eq. 8 for a reflection on a bounded plane,
+// tested once per candidate before any iteration (k_exclude):
+//  - half-space: the outgoing segment leaves on the side of the plane that
+//    the incoming one came from, so the neighbouring points of a reflection
+//    lie on one side of its plane;
+//  - beam: the outgoing ray is the ray from the mirror image of the previous
+//    point through the reflection point, so for the first reflection the
+//    next point lies in the pyramid from TX's image through the rectangle
+//    (likewise for the last reflection with RX's image, backwards).
+// A candidate failing either, with margins, has no path whose points lie
+// inside their objects' bounds (its cost there stays above ~1e-11): it is
+// written as excluded, and the others go, per order, to a list that the
+// solvers iterate.  Margins: an endpoint more than 1e-5 S off the plane, an
+// object wholly more than 1e-6 S off it (the FP64 side table), an object (or
+// RX) wholly more than 1e-5 S outside a face of the pyramid, which is only
+// used when the endpoint is more than 1e-2 S off the plane.
+constexpr int BEAM_F4 = 5;  // float4 per beam: the image point (w: 1 valid), four faces (n, <n, apex>)
+
+__device__ __forceinline__ float plane_dist32(const DevScene& s, int o, const float4& X) {
+  const float4 q0 = __ldg(s.a32 + 4 * o), q3 = __ldg(s.a32 + 4 * o + 3);
+  return dot(mk(q3.x, q3.y, q3.z), mk(X.x - q0.x, X.y - q0.y, X.z - q0.z));
 }
 
-template <int N, class R>
+// Beam of every endpoint e (TX 0..n_tx-1, then RX) through every plane o:
+// beams[(e * n_obj + o) * BEAM_F4 + 0] = (image, valid), + 1 + f = face f
+// (unit normal pointing into the pyramid, <normal, image>), in FP64 rounded
+// to FP32.  Grid: x over objects, y over endpoints.
+__global__ void k_beams(DevScene sc, DevEnds ep, float4* beams, double hmin) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = blockIdx.y;
+  if (o >= sc.n_obj || e >= ep.n_tx + ep.n_rx) return;
+  float4* out = beams + ((int64_t)e * sc.n_obj + o) * BEAM_F4;
+  if (__ldg(sc.kind + o) != K_PLANE) {
+    out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const double* pe = e < ep.n_tx ? ep.tx + 3 * e : ep.rx + 3 * (e - ep.n_tx);
+  const v3<double> P = mk(pe[0], pe[1], pe[2]);
+  const Rec<double> r = load_obj64(sc, o);
+  const v3<double> O = r.f3(0), u = r.f3(4), v = r.f3(8), nrm = r.f3(12);
+  const double h = dot(nrm, P - O);
+  if (!(fabs(h) > hmin)) {
+    out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const v3<double> Pi = axpy(-2.0 * h, nrm, P);
+  const v3<double> C[4] = {O, axpy(r.v[3], u, O), axpy(r.v[7], v, axpy(r.v[3], u, O)), axpy(r.v[7], v, O)};
+  const v3<double> cen = axpy(0.5 * r.v[7], v, axpy(0.5 * r.v[3], u, O));
+  for (int f = 0; f < 4; ++f) {
+    v3<double> nn = cross(C[f] - Pi, C[(f + 1) & 3] - Pi);
+    if (dot(nn, cen - Pi) < 0.0) nn = -nn;
+    nn = nn * (1.0 / sqrt(dot(nn, nn)));
+    out[1 + f] = make_float4((float)nn.x, (float)nn.y, (float)nn.z, (float)dot(nn, Pi));
+  }
+  out[0] = make_float4((float)Pi.x, (float)Pi.y, (float)Pi.z, 1.f);
+}
+
+// Do the points X[0..NP) all lie more than m outside one face of beam b?
+template <int NP>
+__device__ __forceinline__ bool outside_beam(const float4* b, const float4 (&X)[NP], float m) {
+  if (__ldg(&b->w) == 0.f) return false;
+  bool out = false;
+#pragma unroll
+  for (int f = 1; f <= 4; ++f) {
+    const float4 q = __ldg(b + f);
+    bool all = true;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) all = all && fmaf(q.x, X[k].x, fmaf(q.y, X[k].y, q.z * X[k].z)) - q.w < -m;
+    out = out || all;
+  }
+  return out;
+}
+__device__ __forceinline__ void load_vtx(const DevScene& sc, int o, float4 (&V)[8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) V[k] = __ldg(sc.vtx + (int64_t)o * 8 + k);
+}
+
+// The exclusion conditions for a candidate of order n (ids, kinds, endpoint
+// indices), in FP32 on the FP32 endpoint copies.
 __device__ __forceinline__ bool excluded(const DevScene& sc, const DevEnds& ep, const float4* ends32,
-                                         const int (&id)[N], const int (&kind)[N], int it_, int ir_,
-                                         bool exclude) {
-  if (sc.side == nullptr || !exclude) return false;
-  const R m = R(1e-5 * sc.scale);
-  const int n = sc.n_obj;
-  bool ex = false;
+                                         const float4* beams, int n, const int (&id)[4], const int (&kind)[4],
+                                         int it_, int ir_) {
+  const float m_end = (float)(1e-5 * sc.scale), m_beam = (float)(1e-5 * sc.scale);
+  const int no = sc.n_obj;
+  const float4 A = __ldg(ends32 + it_), B = __ldg(ends32 + ep.n_tx + ir_);
+  // the last interaction and the one before it (selects, not indexing)
+  const int idl = n == 1 ? id[0] : n == 2 ? id[1] : n == 3 ? id[2] : id[3];
+  const int kl = n == 1 ? kind[0] : n == 2 ? kind[1] : n == 3 ? kind[2] : kind[3];
+  const int idp = n == 2 ? id[0] : n == 3 ? id[1] : id[2];
   if (kind[0] == K_PLANE) {
-    const R a = plane_dist<R>(sc, id[0], load_end<R>(ep.tx, ends32, it_));
-    if (N == 1) {
-      const R b = plane_dist<R>(sc, id[0], load_end<R>(ep.rx, ends32 + ep.n_tx, ir_));
-      ex = (a > m && b < -m) || (a < -m && b > m);
+    const float a = plane_dist32(sc, id[0], A);
+    const float4* bm = beams + ((int64_t)it_ * no + id[0]) * BEAM_F4;
+    if (n == 1) {
+      const float b = plane_dist32(sc, id[0], B);
+      if ((a > m_end && b < -m_end) || (a < -m_end && b > m_end)) return true;
+      const float4 X[1] = {B};
+      if (outside_beam<1>(bm, X, m_beam)) return true;
     } else {
-      const int cls = __ldg(sc.side + (int64_t)id[0] * n + id[N > 1 ? 1 : 0]);
-      ex = (a > m && cls < 0) || (a < -m && cls > 0);
+      const int cls = __ldg(sc.side + (int64_t)id[0] * no + id[1]);
+      if ((a > m_end && cls < 0) || (a < -m_end && cls > 0)) return true;
+      float4 V[8];
+      load_vtx(sc, id[1], V);
+      if (outside_beam<8>(bm, V, m_beam)) return true;
     }
   }
-  if (N >= 2 && kind[N - 1] == K_PLANE) {
-    const R b = plane_dist<R>(sc, id[N - 1], load_end<R>(ep.rx, ends32 + ep.n_tx, ir_));
-    const int cls = __ldg(sc.side + (int64_t)id[N - 1] * n + id[N >= 2 ? N - 2 : 0]);
-    ex = ex || (b > m && cls < 0) || (b < -m && cls > 0);
+  if (n >= 2 && kl == K_PLANE) {
+    const float b = plane_dist32(sc, idl, B);
+    const int cls = __ldg(sc.side + (int64_t)idl * no + idp);
+    if ((b > m_end && cls < 0) || (b < -m_end && cls > 0)) return true;
+    float4 V[8];
+    load_vtx(sc, idp, V);
+    if (outside_beam<8>(beams + ((int64_t)(ep.n_tx + ir_) * no + idl) * BEAM_F4, V, m_beam)) return true;
   }
 #pragma unroll
-  for (int k = 1; k + 1 < N; ++k)
-    if (kind[k] == K_PLANE) {
-      const int c0 = __ldg(sc.side + (int64_t)id[k] * n + id[k - 1]);
-      const int c1 = __ldg(sc.side + (int64_t)id[k] * n + id[k + 1]);
-      ex = ex || c0 * c1 < 0;
+  for (int k = 1; k < 3; ++k)
+    if (k + 1 < n && kind[k] == K_PLANE) {
+      const int c0 = __ldg(sc.side + (int64_t)id[k] * no + id[k - 1]);
+      const int c1 = __ldg(sc.side + (int64_t)id[k] * no + id[k + 1]);
+      if (c0 * c1 < 0) return true;
     }
-  return ex;
+  return false;
 }
 
 __device__ __forceinline__ void write_excluded(const SolView& out, int64_t c) {
@@ -324,6 +393,60 @@ __device__ __forceinline__ void write_excluded(const SolView& out, int64_t c) {
   out.status[c] = (uint8_t)MPT_PATH_EXCLUDED;
   out.iters[c] = 0;
   out.evals[c] = 0;
+}
+
+// One lane per candidate, a warp on 32 consecutive ones: excluded candidates
+// are written; the others (and records the solvers reject as malformed) are
+// appended to the list of their order range, list[order_begin[o-1] + i] =
+// candidate - order_begin[o-1], counts in list_count[o-1].  One atomic per
+// warp and order keeps a warp's entries together (same object sequence).
+__global__ void __launch_bounds__(256) k_exclude(DevScene sc, DevEnds ep, const float4* ends32, const float4* beams,
+                                                 CandView cv, SolView out, int32_t* list,
+                                                 unsigned long long* list_count) {
+  int64_t ob[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) ob[k] = cv.order_begin[k] < cv.cap ? cv.order_begin[k] : cv.cap;
+  const int64_t total = ob[4];
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < total; w += n_warps) {
+    const int64_t c = w * 32 + lane;
+    int ord = 0;
+    bool keep = false;
+    if (c < total) {
+      ord = 1 + (c >= ob[1]) + (c >= ob[2]) + (c >= ob[3]);
+      const uint4 rr = __ldg(cv.rec + c);
+      const int n = (int)(rr.w & 0xFFu);
+      int id[4], kind[4] = {K_LINE, K_LINE, K_LINE, K_LINE};
+      bool valid = n == ord;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        id[k] = (int)(((k < 2 ? rr.y : rr.z) >> (16 * (k & 1))) & 0xFFFFu);
+        if (k < n) valid = valid && id[k] < sc.n_obj;
+      }
+      int it_, ir_;
+      pair_ends(ep, rr.x, it_, ir_);
+      valid = valid && it_ < ep.n_tx && ir_ < ep.n_rx;
+      if (valid) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (k < n) kind[k] = __ldg(sc.kind + id[k]);
+      }
+      keep = !(valid && excluded(sc, ep, ends32, beams, n, id, kind, it_, ir_));
+      if (!keep) write_excluded(out, c);
+    }
+#pragma unroll
+    for (int o = 1; o <= 4; ++o) {
+      const unsigned m = __ballot_sync(FULL, keep && ord == o);
+      if (m == 0u) continue;
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(list_count + (o - 1), (unsigned long long)__popc(m));
+      base = __shfl_sync(FULL, base, leader);
+      if (keep && ord == o) list[ob[o - 1] + (int64_t)base + __popc(m & lt_mask)] = (int32_t)(c - ob[o - 1]);
+    }
+  }
 }
 
 // ------------------------------------------------------------- kernel A --
@@ -394,7 +517,8 @@ template <int N, int PREC, bool CURVED>
 __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, const float4* ends32,
                                         const CandView& cv, const SolView& out, const SolveCfg& cfg,
                                         unsigned long long* counter, const RefineList& rl, int64_t begin,
-                                        int64_t end, int64_t order_base, uint4 (*rbuf)[GN_CHUNK]) {
+                                        int64_t end, int64_t cand_base, int64_t order_base, const int32_t* list,
+                                        uint4 (*rbuf)[GN_CHUNK], int32_t (*ibuf)[GN_CHUNK]) {
   using R = typename std::conditional<PREC == MPT_FP64_PLAIN, double, float>::type;
   constexpr int Q = 2 * N, P = Q * (Q + 1) / 2;
   const unsigned lane = threadIdx.x & 31;
@@ -444,8 +568,18 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
     }
     len = base < end ? (int)(end - base < size ? end - base : size) : 0;
   };
+  // positions [begin, end) are candidates cand_base + position, or with a
+  // list, candidates cand_base + list[position]
   auto stage = [&](int b, int64_t base, int len) {
-    for (int k = lane; k < len; k += 32) cp_async16(&rbuf[b][k], cv.rec + base + k);
+    for (int k = lane; k < len; k += 32) {
+      if (list != nullptr) {
+        const int32_t v = __ldg(list + base + k);
+        ibuf[b][k] = v;
+        cp_async16(&rbuf[b][k], cv.rec + cand_base + v);
+      } else {
+        cp_async16(&rbuf[b][k], cv.rec + base + k);
+      }
+    }
     cp_async_commit();
   };
   int buf = 0;
@@ -463,7 +597,7 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
     if (idle == FULL || __popc(idle) >= cfg.refill_min) {
       // ---- write the results waiting in idle lanes
       if (done_c >= 0) {
-        const int64_t dc = begin + done_c;
+        const int64_t dc = cand_base + done_c;
 #pragma unroll
         for (int i = 0; i < Q; ++i) out.T[(int64_t)i * out.cap + dc] = to_f64(prm[i]);
         if (out.T32 != nullptr) {
@@ -485,7 +619,7 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
           if (done_push) {
             const int64_t pos = (int64_t)base + __popc(pm & lt_mask);
             const int64_t at = order_base + pos;
-            rl.idx[at] = (int32_t)(begin + done_c - order_base) | (cost < R(PRESCREEN_VIS_COST) ? RL_VIS : 0);
+            rl.idx[at] = (int32_t)(cand_base + done_c - order_base) | (cost < R(PRESCREEN_VIS_COST) ? RL_VIS : 0);
             if (rl.prm != nullptr) {
 #pragma unroll
               for (int i = 0; i < Q; ++i) rl.prm[(int64_t)i * rl.stride + at] = (float)prm[i];
@@ -519,33 +653,23 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
         const int slot = cur_pos + rank;
         cur_pos += nneed < avail ? nneed : avail;
         if (take) {
-          const int64_t idx = cur_base + slot;
+          need = false;
+          const int64_t idx = list != nullptr ? cand_base + ibuf[buf][slot] : cur_base + slot;
           const uint4 rr = rbuf[buf][slot];
           // a record of this solver's order whose objects and endpoints exist
           bool valid = (int)(rr.w & 0xFFu) == N;
-          int id[N], kd[N];
 #pragma unroll
-          for (int k = 0; k < N; ++k) {
-            id[k] = (int)(((k < 2 ? rr.y : rr.z) >> (16 * (k & 1))) & 0xFFFFu);
-            valid = valid && id[k] < sc.n_obj;
-          }
+          for (int k = 0; k < N; ++k)
+            valid = valid && (int)(((k < 2 ? rr.y : rr.z) >> (16 * (k & 1))) & 0xFFFFu) < sc.n_obj;
           int t_, r_;
           pair_ends(ep, rr.x, t_, r_);
           valid = valid && t_ < ep.n_tx && r_ < ep.n_rx;
           if (valid) {
-#pragma unroll
-            for (int k = 0; k < N; ++k) kd[k] = __ldg(sc.kind + id[k]);
-          }
-          if (valid && excluded<N, R>(sc, ep, ends32, id, kd, t_, r_, cfg.exclude)) {
-            // no path: written now; the lane takes another candidate
-            write_excluded(out, idx);
-          } else if (valid) {
-            need = false;
             it_ = t_;
             ir_ = r_;
             // only the record is decoded here; the initial guess is made in
             // the first pass, from the records and endpoints it loads anyway
-            c = (int)(idx - begin);
+            c = (int)(idx - cand_base);
             ids01 = rr.y;
             ids23 = rr.z;
             pair_ = rr.x;
@@ -555,9 +679,10 @@ __device__ __forceinline__ void gn_warp(const DevScene& sc, const DevEnds& ep, c
             lm_ratio = R(cfg.localmin_ratio_planar);
 #pragma unroll
             for (int k = 0; k < N; ++k) {
-              kinds |= kd[k] << (8 * k);
-              pat |= (kd[k] == K_LINE ? 1 : 0) << k;
-              if (CURVED && (kd[k] == K_PARAB || kd[k] == K_ARC)) lm_ratio = R(cfg.localmin_ratio);
+              const int kd = __ldg(sc.kind + (int)(((k < 2 ? rr.y : rr.z) >> (16 * (k & 1))) & 0xFFFFu));
+              kinds |= kd << (8 * k);
+              pat |= (kd == K_LINE ? 1 : 0) << k;
+              if (CURVED && (kd == K_PARAB || kd == K_ARC)) lm_ratio = R(cfg.localmin_ratio);
             }
             fresh = true;
             iters = 0;
@@ -721,13 +846,22 @@ constexpr int gn_min_blocks() {
 template <int N, int PREC, bool CURVED>
 __global__ void __launch_bounds__(SOLVE_BLOCK, gn_min_blocks<N, PREC, CURVED>())
     k_gn(DevScene sc, DevEnds ep, const float4* ends32, CandView cv, SolView out, SolveCfg cfg,
-         unsigned long long* counter, RefineList rl) {
+         unsigned long long* counter, RefineList rl, const int32_t* list, const unsigned long long* list_count) {
   __shared__ __align__(16) uint4 rbuf[GN_WARPS][2][GN_CHUNK];
+  __shared__ int32_t ibuf[GN_WARPS][2][GN_CHUNK];
   int64_t end = cv.order_begin[N];
   if (end > cv.cap) end = cv.cap;
   int64_t begin = cv.order_begin[N - 1];
   if (begin > end) begin = end;
-  gn_warp<N, PREC, CURVED>(sc, ep, ends32, cv, out, cfg, counter, rl, begin, end, begin, rbuf[threadIdx.x >> 5]);
+  if (list != nullptr) {
+    // the candidates of this order that the exclusion pass kept
+    const int64_t n = (int64_t)*list_count < end - begin ? (int64_t)*list_count : end - begin;
+    gn_warp<N, PREC, CURVED>(sc, ep, ends32, cv, out, cfg, counter, rl, 0, n, begin, begin, list + begin,
+                             rbuf[threadIdx.x >> 5], ibuf[threadIdx.x >> 5]);
+  } else {
+    gn_warp<N, PREC, CURVED>(sc, ep, ends32, cv, out, cfg, counter, rl, begin, end, begin, begin, nullptr,
+                             rbuf[threadIdx.x >> 5], ibuf[threadIdx.x >> 5]);
+  }
 }
 
 // One launch over every order (uneven orders and convergence in one
@@ -758,10 +892,10 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_mixed(DevScene sc, DevEnds e
       if (oe <= s) oe = s + 1;
       const int64_t ob = (o >= 1 && o <= 4) ? cv.order_begin[o - 1] : 0;
       switch (o) {
-        case 1: gn_warp<1, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob, rbuf[threadIdx.x >> 5]); break;
-        case 2: gn_warp<2, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob, rbuf[threadIdx.x >> 5]); break;
-        case 3: gn_warp<3, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob, rbuf[threadIdx.x >> 5]); break;
-        case 4: gn_warp<4, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, ob, rbuf[threadIdx.x >> 5]); break;
+        case 1: gn_warp<1, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, s, ob, nullptr, rbuf[threadIdx.x >> 5], nullptr); break;
+        case 2: gn_warp<2, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, s, ob, nullptr, rbuf[threadIdx.x >> 5], nullptr); break;
+        case 3: gn_warp<3, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, s, ob, nullptr, rbuf[threadIdx.x >> 5], nullptr); break;
+        case 4: gn_warp<4, PREC, true>(sc, ep, ends32, cv, out, cfg, nullptr, rl, s, oe, s, ob, nullptr, rbuf[threadIdx.x >> 5], nullptr); break;
         default:
           if (lane == 0) {
             out.cost[s] = (double)INFINITY;
@@ -1305,26 +1439,31 @@ __device__ double gn_f64_lanes(const int (&kind)[N], const Rec<double>& rm, doub
 template <int N, int PREC, bool CURVED>
 __global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_warp(DevScene sc, DevEnds ep, const float4* ends32, CandView cv,
                                                         SolView out, SolveCfg cfg, unsigned long long* counter,
-                                                        RefineList rl) {
+                                                        RefineList rl, const int32_t* list,
+                                                        const unsigned long long* list_count) {
   constexpr int Q = 2 * N, P = Q * (Q + 1) / 2;
   const int lane = (int)(threadIdx.x & 31);
   int64_t end = cv.order_begin[N];
   if (end > cv.cap) end = cv.cap;
   int64_t begin = cv.order_begin[N - 1];
   if (begin > end) begin = end;
+  // positions: candidates begin + position, or begin + list[begin + position]
+  int64_t n_pos = end - begin;
+  if (list != nullptr && (int64_t)*list_count < n_pos) n_pos = (int64_t)*list_count;
   const float c_tol = cfg.c_tol32, step_tol = cfg.step_tol32, mu = cfg.mu32;
   const float diverge = (float)cfg.diverge;
   for (;;) {
     unsigned long long b = 0;
     if (lane == 0) b = atomicAdd(counter, 32ull);
     b = __shfl_sync(FULL, b, 0);
-    const int64_t base = begin + (int64_t)b;
-    if (base >= end) break;
-    const int len = end - base < 32 ? (int)(end - base) : 32;
-    const uint4 mine = lane < len ? __ldg(cv.rec + base + lane) : make_uint4(0u, 0u, 0u, 0u);
+    const int64_t pos = (int64_t)b;
+    if (pos >= n_pos) break;
+    const int len = n_pos - pos < 32 ? (int)(n_pos - pos) : 32;
+    const int32_t off = lane < len ? (list != nullptr ? __ldg(list + begin + pos + lane) : (int32_t)(pos + lane)) : 0;
+    const uint4 mine = lane < len ? __ldg(cv.rec + begin + off) : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll 1
     for (int i = 0; i < len; ++i) {
-      const int64_t c = base + i;
+      const int64_t c = begin + __shfl_sync(FULL, off, i);
       uint4 rr;
       rr.x = __shfl_sync(FULL, mine.x, i);
       rr.y = __shfl_sync(FULL, mine.y, i);
@@ -1356,10 +1495,6 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_gn_warp(DevScene sc, DevEnds ep
       for (int k = 0; k < N; ++k) {
         kind[k] = __ldg(sc.kind + ids[k]);
         if (CURVED && (kind[k] == K_PARAB || kind[k] == K_ARC)) lm_ratio = cfg.localmin_ratio;
-      }
-      if (excluded<N, float>(sc, ep, ends32, ids, kind, it_, ir_, cfg.exclude)) {
-        if (lane == 0) write_excluded(out, c);
-        continue;
       }
       // this lane's object (point lane / 2); lanes past the sequence hold zeros
       Rec<float> rm;
@@ -1686,36 +1821,53 @@ static int grid_for(mpt_ctx* ctx, K kernel, const mpt_schedule* sch, size_t smem
 template <int N, int PREC>
 static void launch_gn(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, const float4* ends32, const CandView& cv,
                       const SolView& sv, const SolveCfg& cfg, const mpt_schedule* sch, RefineList rl, bool curved,
-                      cudaStream_t s) {
+                      const int32_t* list, cudaStream_t s) {
   unsigned long long* counter = ctx->counters + (N - 1);
+  const unsigned long long* list_count = ctx->counters + 28 + (N - 1);
   if constexpr (PREC != MPT_FP64_PLAIN) {
     if (sch != nullptr && ((sch->warp_orders >> (N - 1)) & 1) != 0) {
       if (curved)
         k_gn_warp<N, PREC, true><<<grid_for(ctx, k_gn_warp<N, PREC, true>, sch), SOLVE_BLOCK, 0, s>>>(
-            sc, ep, ends32, cv, sv, cfg, counter, rl);
+            sc, ep, ends32, cv, sv, cfg, counter, rl, list, list_count);
       else
         k_gn_warp<N, PREC, false><<<grid_for(ctx, k_gn_warp<N, PREC, false>, sch), SOLVE_BLOCK, 0, s>>>(
-            sc, ep, ends32, cv, sv, cfg, counter, rl);
+            sc, ep, ends32, cv, sv, cfg, counter, rl, list, list_count);
       return;
     }
   }
   if (curved)
     k_gn<N, PREC, true><<<grid_for(ctx, k_gn<N, PREC, true>, sch), SOLVE_BLOCK, 0, s>>>(sc, ep, ends32, cv, sv, cfg,
-                                                                                       counter, rl);
+                                                                                       counter, rl, list, list_count);
   else
-    k_gn<N, PREC, false><<<grid_for(ctx, k_gn<N, PREC, false>, sch), SOLVE_BLOCK, 0, s>>>(sc, ep, ends32, cv, sv,
-                                                                                         cfg, counter, rl);
+    k_gn<N, PREC, false><<<grid_for(ctx, k_gn<N, PREC, false>, sch), SOLVE_BLOCK, 0, s>>>(
+        sc, ep, ends32, cv, sv, cfg, counter, rl, list, list_count);
 }
 
 template <int PREC>
 static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, const float4* ends32, const CandView& cv,
                        const SolView& sv, const SolveCfg& cfg, const mpt_schedule* sch, RefineList rl,
-                       RefineList rl2, bool curved, cudaStream_t st) {
+                       RefineList rl2, bool curved, int32_t* xlist, float4* beams, cudaStream_t st) {
   // counters[0..3]: per-order candidate cursors; [4]: mixed-order cursor;
   // [8..11]: refine list sizes; [12..15]: sizes after the visibility
   // prescreen; [16..19]: fallback queue sizes; [20..23]: refinement
-  // cursors; [24..27]: prescreen cursors
-  MPT_CUDA_TRY(cudaMemsetAsync(ctx->counters, 0, 28 * sizeof(unsigned long long), st));
+  // cursors; [24..27]: prescreen cursors; [28..31]: sizes of the lists of
+  // candidates the exclusion pass keeps
+  MPT_CUDA_TRY(cudaMemsetAsync(ctx->counters, 0, 32 * sizeof(unsigned long long), st));
+  // the exclusion pass (per-order launches only): beams of every endpoint
+  // through every plane, then one pass over the candidates
+  const int32_t* list = nullptr;
+  if (xlist != nullptr) {
+    const int n_ends = ep.n_tx + ep.n_rx;
+    k_beams<<<dim3((sc.n_obj + 127) / 128, n_ends), 128, 0, st>>>(sc, ep, beams, 1e-2 * sc.scale);
+    MPT_LAUNCH_CHECK();
+    int64_t blocks = (cv.cap + 255) / 256;
+    const int64_t cap_blocks = (int64_t)ctx->sms * 8;
+    if (blocks > cap_blocks) blocks = cap_blocks;
+    if (blocks < 1) blocks = 1;
+    k_exclude<<<(unsigned)blocks, 256, 0, st>>>(sc, ep, ends32, beams, cv, sv, xlist, ctx->counters + 28);
+    MPT_LAUNCH_CHECK();
+    list = xlist;
+  }
   const size_t vsmem = (size_t)sc.n_occ * 96 + (size_t)sc.n_grp * 32;
   // the fallback queue reuses the storage of a list read by then: the first
   // list after the prescreen, else the (unused) second one
@@ -1735,7 +1887,7 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
   {                                                                                                            \
     cudaStream_t s_ = (S);                                                                                     \
     if (per_order) {                                                                                           \
-      launch_gn<N, PREC>(ctx, sc, ep, ends32, cv, sv, cfg, sch, rl, curved, s_);                                \
+      launch_gn<N, PREC>(ctx, sc, ep, ends32, cv, sv, cfg, sch, rl, curved, list, s_);                          \
       MPT_LAUNCH_CHECK();                                                                                      \
     }                                                                                                          \
     if (PREC == MPT_FP32_FP64REFINE) {                                                                         \
@@ -1835,18 +1987,37 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
     ctx->escratch_bytes = ebytes;
   }
   float4* ends32 = reinterpret_cast<float4*>(ctx->escratch);
-  if (precision != MPT_FP64_PLAIN) {
+  // exclusion pass scratch: the per-order lists (4 bytes per candidate) and
+  // the beams of every endpoint through every object (80 bytes each)
+  const bool exclude =
+      cfg.exclude && scene->d.side != nullptr && !(sch && sch->mixed_orders) && n_ends > 0 && n_ends <= 65535;
+  int32_t* xlist = nullptr;
+  float4* beams = nullptr;
+  if (exclude) {
+    const size_t list_bytes = ((size_t)cand->capacity * sizeof(int32_t) + 255) & ~size_t(255);
+    const size_t need = list_bytes + (size_t)n_ends * scene->d.n_obj * BEAM_F4 * sizeof(float4) + 256;
+    if (ctx->xscratch_bytes < need) {
+      if (ctx->xscratch) MPT_CUDA_TRY(cudaFreeAsync(ctx->xscratch, st));
+      ctx->xscratch = nullptr;
+      ctx->xscratch_bytes = 0;
+      MPT_CUDA_TRY(cudaMallocAsync(&ctx->xscratch, need, st));
+      ctx->xscratch_bytes = need;
+    }
+    xlist = reinterpret_cast<int32_t*>(ctx->xscratch);
+    beams = reinterpret_cast<float4*>(static_cast<unsigned char*>(ctx->xscratch) + list_bytes);
+  }
+  if (precision != MPT_FP64_PLAIN || exclude) {
     k_ends_f32<<<(n_ends + 255) / 256, 256, 0, st>>>(ends->tx, ends->n_tx, ends->rx, ends->n_rx, ends32);
     MPT_LAUNCH_CHECK();
   }
   const bool curved = scene_curved(scene);
   switch (precision) {
     case MPT_FP64_PLAIN:
-      return launch_prec<MPT_FP64_PLAIN>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, st);
+      return launch_prec<MPT_FP64_PLAIN>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, xlist, beams, st);
     case MPT_FP32:
-      return launch_prec<MPT_FP32>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, st);
+      return launch_prec<MPT_FP32>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, xlist, beams, st);
     case MPT_FP32_FP64REFINE:
-      return launch_prec<MPT_FP32_FP64REFINE>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, st);
+      return launch_prec<MPT_FP32_FP64REFINE>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, xlist, beams, st);
     default: return MPT_ERR_ARG;
   }
 }

@@ -241,30 +241,82 @@ def fp32_point_error(sc, table, rep: Report, T32: np.ndarray):
     return float(np.where(col, np.abs(X32 - rep.valid_X), 0.0).max())
 
 
-def exclusion_mask(sc, table, m_tx: float = 1e-5, m_obj: float = 1e-6) -> np.ndarray:
-    """Candidates (c = entry * n_pairs + pair) whose reflection on a plane has
-    its two neighbouring points certainly on opposite sides of the plane: the
-    first reflection with TX more than m_tx * S on one side and the next
-    object wholly (every vertex of oracle._object_vertices) more than
-    m_obj * S on the other side (RX for a single reflection), the last
-    reflection likewise with RX and the previous object, an inner reflection
-    with its two neighbouring objects on opposite sides.  Eq. 8 makes the
-    outgoing direction r = i - 2 <i, n> n leave on the side the incoming
-    direction came from, so none of these candidates has a path.  Written
-    from that condition with numpy, independently of the solver's code."""
+def _beams(sc, points: np.ndarray, h_min: float):
+    """For every point P and plane i: the four faces of the pyramid from P's
+    mirror image through rectangle i (unit normals pointing inwards, offsets
+    <n, image>) and whether the pyramid is used (P more than h_min from the
+    plane).  Returns faces [n_points, n_obj, 4, 4] and ok [n_points, n_obj]."""
+    kinds = np.asarray(sc.obj_kind)
+    par = np.asarray(sc.obj_param, np.float64)
+    n = len(kinds)
+    faces = np.zeros((len(points), n, 4, 4))
+    ok = np.zeros((len(points), n), bool)
+    for i in range(n):
+        if kinds[i] != 0:
+            continue
+        nrm, O, u, v, U, V = par[i][0:3], par[i][4:7], par[i][7:10], par[i][10:13], par[i][13], par[i][14]
+        h = (points - O) @ nrm
+        img = points - 2.0 * h[:, None] * nrm
+        C = [O, O + U * u, O + U * u + V * v, O + V * v]
+        cen = O + 0.5 * U * u + 0.5 * V * v
+        for f in range(4):
+            nn = np.cross(C[f] - img, C[(f + 1) % 4] - img)
+            flip = np.einsum("ij,ij->i", nn, cen - img) < 0
+            nn[flip] *= -1.0
+            nn /= np.linalg.norm(nn, axis=1, keepdims=True)
+            faces[:, i, f, :3] = nn
+            faces[:, i, f, 3] = np.einsum("ij,ij->i", nn, img)
+        ok[:, i] = np.abs(h) > h_min
+    return faces, ok
+
+
+def exclusion_mask(sc, table, m_tx: float = 1e-5, m_obj: float = 1e-6, m_beam: float = 1e-5,
+                   h_min: float = 1e-2, beam: bool = True) -> np.ndarray:
+    """Candidates (c = entry * n_pairs + pair) that the reflection law (Eq. 8)
+    rules out before any iteration, written with numpy from the law,
+    independently of the solver's code (margins in units of the scene scale
+    S):
+
+      - half-space: the segment after a reflection leaves on the side of the
+        plane that the segment before it came from.  Excluded: the first
+        reflection with TX more than m_tx from its plane and the next object
+        wholly (every vertex of oracle._object_vertices) more than m_obj on
+        the other side (RX for a single reflection); the last reflection
+        likewise with RX and the previous object; an inner reflection with
+        its two neighbouring objects on opposite sides;
+      - beam (beam=True): the outgoing ray of the first reflection is the ray
+        from TX's mirror image through the reflection point, so the next
+        object (RX for a single reflection) must meet the pyramid from that
+        image through the rectangle; likewise backwards from RX for the last
+        reflection.  Excluded: every vertex more than m_beam outside one face
+        of the pyramid, for an endpoint more than h_min from the plane."""
     kinds = np.asarray(sc.obj_kind)
     par = np.asarray(sc.obj_param, np.float64)
     n = len(kinds)
     verts = [np.asarray(oracle._object_vertices(int(kinds[i]), par[i])) for i in range(n)]
     tx, rx = np.asarray(sc.tx, np.float64), np.asarray(sc.rx, np.float64)
     if sc.pair_mode == 0:
-        A, B = np.repeat(tx, len(rx), axis=0), np.tile(rx, (len(tx), 1))
+        it = np.repeat(np.arange(len(tx)), len(rx))
+        ir = np.tile(np.arange(len(rx)), len(tx))
     else:
-        A, B = tx, rx
-    mt, mo = m_tx * sc.scale, m_obj * sc.scale
+        it = ir = np.arange(len(tx))
+    A, B = tx[it], rx[ir]
+    S = sc.scale
+    mt, mo, mb = m_tx * S, m_obj * S, m_beam * S
+    if beam:
+        fa, oka = _beams(sc, tx, h_min * S)
+        fb, okb = _beams(sc, rx, h_min * S)
 
     def dist(i, X):  # signed distance to plane i: <n, X - O>
         return (X - par[i][4:7]) @ par[i][0:3]
+
+    def outside(faces, ok, X):
+        """faces [k, 4, 4], ok [k], X [k, m, 3] or [m, 3]: all points more
+        than mb outside one face."""
+        d = np.einsum("kfj,mj->kfm", faces[:, :, :3], X) if X.ndim == 2 else \
+            np.einsum("kfj,kmj->kfm", faces[:, :, :3], X)
+        d = d - faces[:, :, 3][:, :, None]
+        return ok & np.any(np.all(d < -mb, axis=2), axis=1)
 
     side = np.zeros((n, n), np.int8)  # +1 / -1: object j wholly in front of / behind plane i
     for i in range(n):
@@ -284,13 +336,19 @@ def exclusion_mask(sc, table, m_tx: float = 1e-5, m_obj: float = 1e-6) -> np.nda
             if o == 1:
                 b = dist(ids[0], B)
                 ex |= ((a > mt) & (b < -mt)) | ((a < -mt) & (b > mt))
+                if beam:
+                    ex |= outside(fa[it, ids[0]], oka[it, ids[0]], B[:, None, :])
             else:
                 s = side[ids[0], ids[1]]
                 ex |= ((a > mt) & (s < 0)) | ((a < -mt) & (s > 0))
+                if beam:
+                    ex |= outside(fa[it, ids[0]], oka[it, ids[0]], verts[ids[1]])
         if o >= 2 and kinds[ids[-1]] == 0:
             b = dist(ids[-1], B)
             s = side[ids[-1], ids[-2]]
             ex |= ((b > mt) & (s < 0)) | ((b < -mt) & (s > 0))
+            if beam:
+                ex |= outside(fb[ir, ids[-1]], okb[ir, ids[-1]], verts[ids[-2]])
         for k in range(1, o - 1):
             if kinds[ids[k]] == 0 and int(side[ids[k], ids[k - 1]]) * int(side[ids[k], ids[k + 1]]) < 0:
                 ex[:] = True
