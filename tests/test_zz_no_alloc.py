@@ -79,15 +79,16 @@ def test_noalloc_rejects_more_candidates_than_its_array_serves(mpt):
 
 
 def test_noalloc_groups_beyond_its_list_match_validate(mpt):
-    # FP64-plain solutions mark every candidate as final, so the converged
-    # ones (about 400k of 602k here) exceed the fixed list of 2^18 entries:
-    # the groups that do not fit are tested in full by the overflow kernel
+    # FP64-plain solutions mark every candidate as final, so with every
+    # candidate iterated (the solver's exclusion pass off) the converged ones
+    # (about 400k of 602k here) exceed the fixed list of 2^18 entries: the
+    # groups that do not fit are tested in full by the overflow kernel
     ctx = mpt.Context(0)
     stream = torch.cuda.current_stream()
     sc = S.urban_block(8)
     ds = mpt.DeviceScene(ctx, sc)
     cands = mpt.enumerate_candidates(ds, 2, S.CONFIG_SPECS["urban_block"])
-    sols = mpt.solve(ds, cands, mpt.FP64_PLAIN)
+    sols = mpt.solve(ds, cands, mpt.FP64_PLAIN, mpt.schedule_struct(exclude=2))
     listed = int(((sols.status.to(torch.int32) & mpt.PATH_REFINED) != 0).logical_and(sols.cost < mpt.TAU).sum())
     assert listed > (1 << 18)
     want = mpt.validate(ds, cands, sols, capacity=cands.capacity)
