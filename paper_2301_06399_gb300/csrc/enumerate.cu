@@ -434,7 +434,8 @@ __global__ void k_side_table(DevScene sc, double delta, int8_t* side) {
 }
 
 // vtx[o][k]: the points of object_vertices in FP32, the last one repeated
-// up to 8 (a repeated point changes no test over all of them).
+// up to 8 (a repeated point changes no test over all of them); w holds the
+// number of distinct points.
 __global__ void k_vertices(DevScene sc, float4* vtx) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= sc.n_obj) return;
@@ -442,7 +443,7 @@ __global__ void k_vertices(DevScene sc, float4* vtx) {
   const int m = object_vertices(sc, o, x);
   for (int k = 0; k < 8; ++k) {
     const v3<double>& p = x[k < m ? k : m - 1];
-    vtx[(int64_t)o * 8 + k] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.f);
+    vtx[(int64_t)o * 8 + k] = make_float4((float)p.x, (float)p.y, (float)p.z, (float)m);
   }
 }
 

@@ -34,7 +34,8 @@ struct DevScene {
   const int8_t* side;       // [n_obj][n_obj] or null: side[i*n_obj + j] = +1 (-1) when object j lies wholly
                             // more than 1e-6 S in front of (behind) plane i, else 0 (0 for non-planes i)
   const float4* vtx;        // [n_obj][8] or null: FP32 points whose convex hull holds the object (rectangle
-                            // corners, edge ends, paraboloid box corners, arc square corners; the last repeated)
+                            // corners, edge ends, paraboloid box corners, arc square corners; the last repeated;
+                            // w = the number of distinct points)
   double scale;
 };
 

@@ -281,7 +281,7 @@ __device__ __forceinline__ Rec<R> load_obj_kind(const DevScene& s, int o) {
 // object wholly more than 1e-6 S off it (the FP64 side table), an object (or
 // RX) wholly more than 1e-5 S outside a face of the pyramid, which is only
 // used when the endpoint is more than 1e-2 S off the plane.
-constexpr int BEAM_F4 = 5;  // float4 per beam: the image point (w: 1 valid), four faces (n, <n, apex>)
+constexpr int BEAM_F4 = 5;  // float4 per (endpoint, object): image and signed distance, four faces (n, <n, apex>)
 
 __device__ __forceinline__ float plane_dist32(const DevScene& s, int o, const float4& X) {
   const float4 q0 = __ldg(s.a32 + 4 * o), q3 = __ldg(s.a32 + 4 * o + 3);
@@ -289,43 +289,43 @@ __device__ __forceinline__ float plane_dist32(const DevScene& s, int o, const fl
 }
 
 // Beam of every endpoint e (TX 0..n_tx-1, then RX) through every plane o:
-// beams[(e * n_obj + o) * BEAM_F4 + 0] = (image, valid), + 1 + f = face f
-// (unit normal pointing into the pyramid, <normal, image>), in FP64 rounded
-// to FP32.  Grid: x over objects, y over endpoints.
-__global__ void k_beams(DevScene sc, DevEnds ep, float4* beams, double hmin) {
+// beams[(e * n_obj + o) * BEAM_F4 + 0] = (image of e in the plane, signed
+// distance h of e from the plane), + 1 + f = face f of the pyramid from the
+// image through the rectangle (unit normal pointing into it, <normal,
+// image>).  FP32, with the geometry taken relative to the rectangle's origin
+// (magnitudes of the scene's size: rounding ~1e-5 m, a hundredth of the
+// margins).  Non-planes get h = 0.  Grid: x over objects, y over endpoints.
+__global__ void k_beams(DevScene sc, const float4* ends32, int n_ends, float4* beams) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   const int e = blockIdx.y;
-  if (o >= sc.n_obj || e >= ep.n_tx + ep.n_rx) return;
+  if (o >= sc.n_obj || e >= n_ends) return;
   float4* out = beams + ((int64_t)e * sc.n_obj + o) * BEAM_F4;
   if (__ldg(sc.kind + o) != K_PLANE) {
     out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
-  const double* pe = e < ep.n_tx ? ep.tx + 3 * e : ep.rx + 3 * (e - ep.n_tx);
-  const v3<double> P = mk(pe[0], pe[1], pe[2]);
-  const Rec<double> r = load_obj64(sc, o);
-  const v3<double> O = r.f3(0), u = r.f3(4), v = r.f3(8), nrm = r.f3(12);
-  const double h = dot(nrm, P - O);
-  if (!(fabs(h) > hmin)) {
-    out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-    return;
-  }
-  const v3<double> Pi = axpy(-2.0 * h, nrm, P);
-  const v3<double> C[4] = {O, axpy(r.v[3], u, O), axpy(r.v[7], v, axpy(r.v[3], u, O)), axpy(r.v[7], v, O)};
-  const v3<double> cen = axpy(0.5 * r.v[7], v, axpy(0.5 * r.v[3], u, O));
+  const Rec<float> r = load_obj32a(sc, o);
+  const v3<float> O = r.f3(0), u = r.f3(4), v = r.f3(8), nrm = r.f3(12);
+  const float4 pe = __ldg(ends32 + e);
+  const v3<float> p = mk(pe.x, pe.y, pe.z) - O;  // the endpoint relative to O
+  const float h = dot(nrm, p);
+  const v3<float> pi = axpy(-2.0f * h, nrm, p);  // its image, relative to O
+  const v3<float> C[4] = {mk(0.f, 0.f, 0.f), u * r.v[3], axpy(r.v[7], v, u * r.v[3]), v * r.v[7]};
+  const v3<float> cen = axpy(0.5f * r.v[7], v, u * (0.5f * r.v[3]));
+#pragma unroll
   for (int f = 0; f < 4; ++f) {
-    v3<double> nn = cross(C[f] - Pi, C[(f + 1) & 3] - Pi);
-    if (dot(nn, cen - Pi) < 0.0) nn = -nn;
-    nn = nn * (1.0 / sqrt(dot(nn, nn)));
-    out[1 + f] = make_float4((float)nn.x, (float)nn.y, (float)nn.z, (float)dot(nn, Pi));
+    v3<float> nn = cross(C[f] - pi, C[(f + 1) & 3] - pi);
+    if (dot(nn, cen - pi) < 0.f) nn = -nn;
+    nn = nn * rsqrtf(dot(nn, nn));
+    // offset in absolute coordinates: <n, O> + <n, image - O>
+    out[1 + f] = make_float4(nn.x, nn.y, nn.z, dot(nn, O) + dot(nn, pi));
   }
-  out[0] = make_float4((float)Pi.x, (float)Pi.y, (float)Pi.z, 1.f);
+  out[0] = make_float4(pi.x + O.x, pi.y + O.y, pi.z + O.z, h);
 }
 
 // Do the points X[0..NP) all lie more than m outside one face of beam b?
 template <int NP>
 __device__ __forceinline__ bool outside_beam(const float4* b, const float4 (&X)[NP], float m) {
-  if (__ldg(&b->w) == 0.f) return false;
   bool out = false;
 #pragma unroll
   for (int f = 1; f <= 4; ++f) {
@@ -337,47 +337,94 @@ __device__ __forceinline__ bool outside_beam(const float4* b, const float4 (&X)[
   }
   return out;
 }
-__device__ __forceinline__ void load_vtx(const DevScene& sc, int o, float4 (&V)[8]) {
+
+// Exclusion bits of a reflection on plane a next to endpoint e (TX before
+// the first reflection, RX after the last) and a neighbouring object b:
+// xbits[(e * n_obj + a) * words + b / 32] bit b % 32 set when the
+// half-space or the beam condition rules b out.  A lane holds one object b
+// (its distinct vertices in registers) and a warp one word of 32 objects;
+// the warp walks a range of (e, a) pairs, whose beam faces are the same for
+// every lane (broadcast loads that do not depend on one another).
+constexpr int XBITS_PAIRS = 64;  // (e, a) pairs a warp walks
+
+__global__ void __launch_bounds__(128) k_exclusion_bits(DevScene sc, const float4* beams, int n_ends, int words,
+                                                        uint32_t* xbits, float m_end, float m_beam, float h_min) {
+  const int lane = threadIdx.x & 31;
+  const int no = sc.n_obj;
+  const int64_t total = (int64_t)n_ends * no;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int w = (int)(gw % words);                       // the word: objects 32 w ..
+  const int64_t q0 = (gw / words) * XBITS_PAIRS;         // the first (e, a) pair
+  if (q0 >= total) return;                               // warp-uniform
+  const int b = w * 32 + lane;
+  float4 V[8];
+  int nv = 0;
+  if (b < no) {
 #pragma unroll
-  for (int k = 0; k < 8; ++k) V[k] = __ldg(sc.vtx + (int64_t)o * 8 + k);
+    for (int k = 0; k < 8; ++k) V[k] = __ldg(sc.vtx + (int64_t)b * 8 + k);
+    nv = (int)V[0].w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) V[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  int a = (int)(q0 % no);
+  const int64_t q1 = q0 + XBITS_PAIRS < total ? q0 + XBITS_PAIRS : total;
+  for (int64_t q = q0; q < q1; ++q) {
+    bool ex = false;
+    if (__ldg(sc.kind + a) == K_PLANE && b < no && b != a) {
+      const float4* bm = beams + q * BEAM_F4;
+      const float h = __ldg(&bm->w);
+      const int cls = __ldg(sc.side + (int64_t)a * no + b);
+      ex = (h > m_end && cls < 0) || (h < -m_end && cls > 0);
+      if (fabsf(h) > h_min) {
+#pragma unroll
+        for (int f = 1; f <= 4; ++f) {
+          const float4 fq = __ldg(bm + f);
+          bool all = true;
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            all = all && (k >= nv || fmaf(fq.x, V[k].x, fmaf(fq.y, V[k].y, fq.z * V[k].z)) - fq.w < -m_beam);
+          ex = ex || all;
+        }
+      }
+    }
+    const unsigned m = __ballot_sync(FULL, ex);
+    if (lane == 0) xbits[q * words + w] = m;
+    if (++a == no) a = 0;
+  }
+}
+
+__device__ __forceinline__ bool xbit(const uint32_t* xbits, int words, int64_t e, int no, int a, int b) {
+  return (__ldg(xbits + (e * no + a) * words + (b >> 5)) >> (b & 31)) & 1u;
 }
 
 // The exclusion conditions for a candidate of order n (ids, kinds, endpoint
-// indices), in FP32 on the FP32 endpoint copies.
+// indices): table lookups for the first and last reflections, the endpoint
+// test of a single reflection, the side table for inner reflections.
 __device__ __forceinline__ bool excluded(const DevScene& sc, const DevEnds& ep, const float4* ends32,
-                                         const float4* beams, int n, const int (&id)[4], const int (&kind)[4],
-                                         int it_, int ir_) {
+                                         const float4* beams, const uint32_t* xbits, int words, int n,
+                                         const int (&id)[4], const int (&kind)[4], int it_, int ir_) {
   const float m_end = (float)(1e-5 * sc.scale), m_beam = (float)(1e-5 * sc.scale);
+  const float h_min = (float)(1e-2 * sc.scale);
   const int no = sc.n_obj;
-  const float4 A = __ldg(ends32 + it_), B = __ldg(ends32 + ep.n_tx + ir_);
   // the last interaction and the one before it (selects, not indexing)
   const int idl = n == 1 ? id[0] : n == 2 ? id[1] : n == 3 ? id[2] : id[3];
   const int kl = n == 1 ? kind[0] : n == 2 ? kind[1] : n == 3 ? kind[2] : kind[3];
   const int idp = n == 2 ? id[0] : n == 3 ? id[1] : id[2];
   if (kind[0] == K_PLANE) {
-    const float a = plane_dist32(sc, id[0], A);
-    const float4* bm = beams + ((int64_t)it_ * no + id[0]) * BEAM_F4;
     if (n == 1) {
+      const float4* bm = beams + ((int64_t)it_ * no + id[0]) * BEAM_F4;
+      const float a = __ldg(&bm->w);
+      const float4 B = __ldg(ends32 + ep.n_tx + ir_);
       const float b = plane_dist32(sc, id[0], B);
       if ((a > m_end && b < -m_end) || (a < -m_end && b > m_end)) return true;
       const float4 X[1] = {B};
-      if (outside_beam<1>(bm, X, m_beam)) return true;
-    } else {
-      const int cls = __ldg(sc.side + (int64_t)id[0] * no + id[1]);
-      if ((a > m_end && cls < 0) || (a < -m_end && cls > 0)) return true;
-      float4 V[8];
-      load_vtx(sc, id[1], V);
-      if (outside_beam<8>(bm, V, m_beam)) return true;
+      if (fabsf(a) > h_min && outside_beam<1>(bm, X, m_beam)) return true;
+    } else if (xbit(xbits, words, it_, no, id[0], id[1])) {
+      return true;
     }
   }
-  if (n >= 2 && kl == K_PLANE) {
-    const float b = plane_dist32(sc, idl, B);
-    const int cls = __ldg(sc.side + (int64_t)idl * no + idp);
-    if ((b > m_end && cls < 0) || (b < -m_end && cls > 0)) return true;
-    float4 V[8];
-    load_vtx(sc, idp, V);
-    if (outside_beam<8>(beams + ((int64_t)(ep.n_tx + ir_) * no + idl) * BEAM_F4, V, m_beam)) return true;
-  }
+  if (n >= 2 && kl == K_PLANE && xbit(xbits, words, (int64_t)ep.n_tx + ir_, no, idl, idp)) return true;
 #pragma unroll
   for (int k = 1; k < 3; ++k)
     if (k + 1 < n && kind[k] == K_PLANE) {
@@ -395,14 +442,18 @@ __device__ __forceinline__ void write_excluded(const SolView& out, int64_t c) {
   out.evals[c] = 0;
 }
 
-// One lane per candidate, a warp on 32 consecutive ones: excluded candidates
-// are written; the others (and records the solvers reject as malformed) are
-// appended to the list of their order range, list[order_begin[o-1] + i] =
-// candidate - order_begin[o-1], counts in list_count[o-1].  One atomic per
-// warp and order keeps a warp's entries together (same object sequence).
+// Eight candidates per lane, a warp on 256 consecutive ones per iteration:
+// excluded candidates are written; the others (and records the solvers
+// reject as malformed) are appended to the list of their order range,
+// list[order_begin[o-1] + i] = candidate - order_begin[o-1], counts in
+// list_count[o-1], in candidate order within the warp's 256.  The appends
+// of the 256 take one atomic per order present (one counter takes every
+// append, so its atomics would otherwise bound the pass).
+constexpr int XC_PER_LANE = 8;
+
 __global__ void __launch_bounds__(256) k_exclude(DevScene sc, DevEnds ep, const float4* ends32, const float4* beams,
-                                                 CandView cv, SolView out, int32_t* list,
-                                                 unsigned long long* list_count) {
+                                                 const uint32_t* xbits, int words, CandView cv, SolView out,
+                                                 int32_t* list, unsigned long long* list_count) {
   int64_t ob[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) ob[k] = cv.order_begin[k] < cv.cap ? cv.order_begin[k] : cv.cap;
@@ -410,41 +461,61 @@ __global__ void __launch_bounds__(256) k_exclude(DevScene sc, DevEnds ep, const 
   const unsigned lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < total; w += n_warps) {
-    const int64_t c = w * 32 + lane;
-    int ord = 0;
-    bool keep = false;
-    if (c < total) {
-      ord = 1 + (c >= ob[1]) + (c >= ob[2]) + (c >= ob[3]);
-      const uint4 rr = __ldg(cv.rec + c);
-      const int n = (int)(rr.w & 0xFFu);
-      int id[4], kind[4] = {K_LINE, K_LINE, K_LINE, K_LINE};
-      bool valid = n == ord;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 * XC_PER_LANE < total;
+       w += n_warps) {
+    const int64_t c0 = w * 32 * XC_PER_LANE + lane;
+    uint32_t keep_bits = 0;  // bit j: candidate c0 + 32 j is kept
+    int ord_of[XC_PER_LANE];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        id[k] = (int)(((k < 2 ? rr.y : rr.z) >> (16 * (k & 1))) & 0xFFFFu);
-        if (k < n) valid = valid && id[k] < sc.n_obj;
-      }
-      int it_, ir_;
-      pair_ends(ep, rr.x, it_, ir_);
-      valid = valid && it_ < ep.n_tx && ir_ < ep.n_rx;
-      if (valid) {
+    for (int j = 0; j < XC_PER_LANE; ++j) {
+      const int64_t c = c0 + 32 * j;
+      ord_of[j] = 0;
+      if (c < total) {
+        const int ord = 1 + (c >= ob[1]) + (c >= ob[2]) + (c >= ob[3]);
+        ord_of[j] = ord;
+        const uint4 rr = __ldg(cv.rec + c);
+        const int n = (int)(rr.w & 0xFFu);
+        int id[4], kind[4] = {K_LINE, K_LINE, K_LINE, K_LINE};
+        bool valid = n == ord;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (k < n) kind[k] = __ldg(sc.kind + id[k]);
+        for (int k = 0; k < 4; ++k) {
+          id[k] = (int)(((k < 2 ? rr.y : rr.z) >> (16 * (k & 1))) & 0xFFFFu);
+          if (k < n) valid = valid && id[k] < sc.n_obj;
+        }
+        int it_, ir_;
+        pair_ends(ep, rr.x, it_, ir_);
+        valid = valid && it_ < ep.n_tx && ir_ < ep.n_rx;
+        if (valid) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (k < n) kind[k] = __ldg(sc.kind + id[k]);
+        }
+        if (valid && excluded(sc, ep, ends32, beams, xbits, words, n, id, kind, it_, ir_))
+          write_excluded(out, c);
+        else
+          keep_bits |= 1u << j;
       }
-      keep = !(valid && excluded(sc, ep, ends32, beams, n, id, kind, it_, ir_));
-      if (!keep) write_excluded(out, c);
     }
+    // appends: per order present, one atomic for the warp's 256
 #pragma unroll
     for (int o = 1; o <= 4; ++o) {
-      const unsigned m = __ballot_sync(FULL, keep && ord == o);
-      if (m == 0u) continue;
-      const int leader = __ffs(m) - 1;
+      unsigned m[XC_PER_LANE];
+      int cnt = 0;
+#pragma unroll
+      for (int j = 0; j < XC_PER_LANE; ++j) {
+        m[j] = __ballot_sync(FULL, ((keep_bits >> j) & 1u) && ord_of[j] == o);
+        cnt += __popc(m[j]);
+      }
+      if (cnt == 0) continue;
       unsigned long long base = 0;
-      if ((int)lane == leader) base = atomicAdd(list_count + (o - 1), (unsigned long long)__popc(m));
-      base = __shfl_sync(FULL, base, leader);
-      if (keep && ord == o) list[ob[o - 1] + (int64_t)base + __popc(m & lt_mask)] = (int32_t)(c - ob[o - 1]);
+      if (lane == 0) base = atomicAdd(list_count + (o - 1), (unsigned long long)cnt);
+      base = __shfl_sync(FULL, base, 0);
+#pragma unroll
+      for (int j = 0; j < XC_PER_LANE; ++j) {
+        if ((m[j] >> lane) & 1u)
+          list[ob[o - 1] + (int64_t)base + __popc(m[j] & lt_mask)] = (int32_t)(c0 + 32 * j - ob[o - 1]);
+        base += __popc(m[j]);
+      }
     }
   }
 }
@@ -1846,7 +1917,8 @@ static void launch_gn(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, const
 template <int PREC>
 static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, const float4* ends32, const CandView& cv,
                        const SolView& sv, const SolveCfg& cfg, const mpt_schedule* sch, RefineList rl,
-                       RefineList rl2, bool curved, int32_t* xlist, float4* beams, cudaStream_t st) {
+                       RefineList rl2, bool curved, int32_t* xlist, float4* beams, uint32_t* xbits,
+                       cudaStream_t st) {
   // counters[0..3]: per-order candidate cursors; [4]: mixed-order cursor;
   // [8..11]: refine list sizes; [12..15]: sizes after the visibility
   // prescreen; [16..19]: fallback queue sizes; [20..23]: refinement
@@ -1858,13 +1930,20 @@ static int launch_prec(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, cons
   const int32_t* list = nullptr;
   if (xlist != nullptr) {
     const int n_ends = ep.n_tx + ep.n_rx;
-    k_beams<<<dim3((sc.n_obj + 127) / 128, n_ends), 128, 0, st>>>(sc, ep, beams, 1e-2 * sc.scale);
+    const int words = (sc.n_obj + 31) / 32;
+    k_beams<<<dim3((sc.n_obj + 127) / 128, n_ends), 128, 0, st>>>(sc, ends32, n_ends, beams);
+    MPT_LAUNCH_CHECK();
+    const int64_t xwarps = ((int64_t)n_ends * sc.n_obj + XBITS_PAIRS - 1) / XBITS_PAIRS * words;
+    k_exclusion_bits<<<(unsigned)((xwarps + 3) / 4), 128, 0, st>>>(sc, beams, n_ends, words, xbits,
+                                                                 (float)(1e-5 * sc.scale), (float)(1e-5 * sc.scale),
+                                                                 (float)(1e-2 * sc.scale));
     MPT_LAUNCH_CHECK();
     int64_t blocks = (cv.cap + 255) / 256;
     const int64_t cap_blocks = (int64_t)ctx->sms * 8;
     if (blocks > cap_blocks) blocks = cap_blocks;
     if (blocks < 1) blocks = 1;
-    k_exclude<<<(unsigned)blocks, 256, 0, st>>>(sc, ep, ends32, beams, cv, sv, xlist, ctx->counters + 28);
+    k_exclude<<<(unsigned)blocks, 256, 0, st>>>(sc, ep, ends32, beams, xbits, words, cv, sv, xlist,
+                                                 ctx->counters + 28);
     MPT_LAUNCH_CHECK();
     list = xlist;
   }
@@ -1987,15 +2066,20 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
     ctx->escratch_bytes = ebytes;
   }
   float4* ends32 = reinterpret_cast<float4*>(ctx->escratch);
-  // exclusion pass scratch: the per-order lists (4 bytes per candidate) and
-  // the beams of every endpoint through every object (80 bytes each)
-  const bool exclude =
-      cfg.exclude && scene->d.side != nullptr && !(sch && sch->mixed_orders) && n_ends > 0 && n_ends <= 65535;
+  // exclusion pass scratch: the per-order lists (4 bytes per candidate),
+  // the beams of every endpoint through every object (80 bytes each) and the
+  // exclusion bits of every (endpoint, plane, object)
+  const size_t n_eo = (size_t)n_ends * scene->d.n_obj;
+  const size_t bits_bytes = ((n_eo * ((scene->d.n_obj + 31) / 32) * sizeof(uint32_t)) + 255) & ~size_t(255);
+  const bool exclude = cfg.exclude && scene->d.side != nullptr && !(sch && sch->mixed_orders) && n_ends > 0 &&
+                       n_ends <= 65535 && bits_bytes <= ((size_t)1 << 28);
   int32_t* xlist = nullptr;
   float4* beams = nullptr;
+  uint32_t* xbits = nullptr;
   if (exclude) {
     const size_t list_bytes = ((size_t)cand->capacity * sizeof(int32_t) + 255) & ~size_t(255);
-    const size_t need = list_bytes + (size_t)n_ends * scene->d.n_obj * BEAM_F4 * sizeof(float4) + 256;
+    const size_t beam_bytes = (n_eo * BEAM_F4 * sizeof(float4) + 255) & ~size_t(255);
+    const size_t need = list_bytes + beam_bytes + bits_bytes + 256;
     if (ctx->xscratch_bytes < need) {
       if (ctx->xscratch) MPT_CUDA_TRY(cudaFreeAsync(ctx->xscratch, st));
       ctx->xscratch = nullptr;
@@ -2005,6 +2089,7 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
     }
     xlist = reinterpret_cast<int32_t*>(ctx->xscratch);
     beams = reinterpret_cast<float4*>(static_cast<unsigned char*>(ctx->xscratch) + list_bytes);
+    xbits = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(ctx->xscratch) + list_bytes + beam_bytes);
   }
   if (precision != MPT_FP64_PLAIN || exclude) {
     k_ends_f32<<<(n_ends + 255) / 256, 256, 0, st>>>(ends->tx, ends->n_tx, ends->rx, ends->n_rx, ends32);
@@ -2013,11 +2098,14 @@ int launch_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends
   const bool curved = scene_curved(scene);
   switch (precision) {
     case MPT_FP64_PLAIN:
-      return launch_prec<MPT_FP64_PLAIN>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, xlist, beams, st);
+      return launch_prec<MPT_FP64_PLAIN>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, xlist, beams, xbits,
+                                    st);
     case MPT_FP32:
-      return launch_prec<MPT_FP32>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, xlist, beams, st);
+      return launch_prec<MPT_FP32>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, xlist, beams, xbits,
+                                    st);
     case MPT_FP32_FP64REFINE:
-      return launch_prec<MPT_FP32_FP64REFINE>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, xlist, beams, st);
+      return launch_prec<MPT_FP32_FP64REFINE>(ctx, scene->d, ep, ends32, cv, sv, cfg, sch, rl, rl2, curved, xlist, beams, xbits,
+                                    st);
     default: return MPT_ERR_ARG;
   }
 }
