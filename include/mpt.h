@@ -228,6 +228,17 @@ int mpt_ctx_create(int device, mpt_ctx** out);
 int mpt_ctx_destroy(mpt_ctx* ctx);
 /* Number of SMs of the context's device (host value). */
 int mpt_ctx_sm_count(const mpt_ctx* ctx);
+/* Opt-in timing of the solver kernel of each path order (measurement only;
+ * the paper has no counterpart).  With on != 0, every later mpt_solve with
+ * per-order launches records a pair of CUDA events around the launch of each
+ * order's solver, on the stream that launch uses; mpt_ctx_solver_ms writes
+ * the elapsed milliseconds of the last such launch of `order` (1..4) once the
+ * caller has synchronised it.  Off by default; keep it off while capturing a
+ * CUDA graph.  Errors: MPT_ERR_ARG (null context or output, order out of
+ * range, timing never switched on), MPT_ERR_CUDA (events not created, or
+ * not recorded / not complete). */
+int mpt_ctx_time_solver(mpt_ctx* ctx, int on);
+int mpt_ctx_solver_ms(mpt_ctx* ctx, int order, float* ms);
 
 /* ------------------------------------------------------------------ scene */
 

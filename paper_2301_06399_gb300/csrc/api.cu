@@ -136,6 +136,8 @@ int mpt_ctx_create(int device, mpt_ctx** out) {
   c->xscratch = nullptr;
   c->xscratch_bytes = 0;
   c->tune_cache = nullptr;
+  c->time_solver = false;
+  c->ev_gn_made = false;
   *out = c;
   return MPT_OK;
 }
@@ -154,12 +156,40 @@ int mpt_ctx_destroy(mpt_ctx* ctx) {
     cudaEventDestroy(ctx->ev_join[i]);
   }
   cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_gn_made)
+    for (int o = 0; o < 4; ++o)
+      for (int k = 0; k < 2; ++k) cudaEventDestroy(ctx->ev_gn[o][k]);
   mpt::tune_cache_free(ctx);
   delete ctx;
   return MPT_OK;
 }
 
 int mpt_ctx_sm_count(const mpt_ctx* ctx) { return ctx ? ctx->sms : 0; }
+
+int mpt_ctx_time_solver(mpt_ctx* ctx, int on) {
+  if (!ctx) return MPT_ERR_ARG;
+  if (on && !ctx->ev_gn_made) {
+    MPT_CUDA_TRY(cudaSetDevice(ctx->device));
+    for (int o = 0; o < 4; ++o)
+      for (int k = 0; k < 2; ++k)
+        if (cudaEventCreate(&ctx->ev_gn[o][k]) != cudaSuccess) {
+          for (int q = 0; q < 2 * o + k; ++q) cudaEventDestroy(ctx->ev_gn[q / 2][q % 2]);
+          return MPT_ERR_CUDA;
+        }
+    ctx->ev_gn_made = true;
+  }
+  ctx->time_solver = on != 0;
+  return MPT_OK;
+}
+
+int mpt_ctx_solver_ms(mpt_ctx* ctx, int order, float* ms) {
+  if (!ctx || !ms || order < 1 || order > 4 || !ctx->ev_gn_made) return MPT_ERR_ARG;
+  if (cudaEventElapsedTime(ms, ctx->ev_gn[order - 1][0], ctx->ev_gn[order - 1][1]) != cudaSuccess) {
+    cudaGetLastError();
+    return MPT_ERR_CUDA;
+  }
+  return MPT_OK;
+}
 
 int mpt_ctx_check(mpt_ctx* ctx, void* stream) {
   if (!ctx) return MPT_ERR_ARG;

@@ -202,6 +202,10 @@ struct mpt_ctx {
   cudaEvent_t ev_fork, ev_join[3];
   // schedules chosen by mpt_autotune, by workload signature (tune.cu)
   void* tune_cache;
+  // opt-in timing of each order's solver launch (mpt_ctx_time_solver)
+  bool time_solver;
+  bool ev_gn_made;
+  cudaEvent_t ev_gn[4][2];
 };
 
 // Makes the auxiliary streams wait for the work enqueued on st so far.

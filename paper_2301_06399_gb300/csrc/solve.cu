@@ -1886,6 +1886,12 @@ static int grid_for(mpt_ctx* ctx, K kernel, const mpt_schedule* sch, size_t smem
   return ctx->sms * occ;
 }
 
+template <int N, int PREC>
+static void launch_gn_kernel(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, const float4* ends32,
+                             const CandView& cv, const SolView& sv, const SolveCfg& cfg, const mpt_schedule* sch,
+                             RefineList rl, bool curved, const int32_t* list, const unsigned long long* list_count,
+                             unsigned long long* counter, cudaStream_t s);
+
 // The solver of order N: one candidate per lane (k_gn), or one per warp
 // (k_gn_warp) for the orders the schedule's warp_orders names (FP32
 // precisions only).
@@ -1895,6 +1901,16 @@ static void launch_gn(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, const
                       const int32_t* list, cudaStream_t s) {
   unsigned long long* counter = ctx->counters + (N - 1);
   const unsigned long long* list_count = ctx->counters + 28 + (N - 1);
+  if (ctx->time_solver) cudaEventRecord(ctx->ev_gn[N - 1][0], s);
+  launch_gn_kernel<N, PREC>(ctx, sc, ep, ends32, cv, sv, cfg, sch, rl, curved, list, list_count, counter, s);
+  if (ctx->time_solver) cudaEventRecord(ctx->ev_gn[N - 1][1], s);
+}
+
+template <int N, int PREC>
+static void launch_gn_kernel(mpt_ctx* ctx, const DevScene& sc, const DevEnds& ep, const float4* ends32,
+                             const CandView& cv, const SolView& sv, const SolveCfg& cfg, const mpt_schedule* sch,
+                             RefineList rl, bool curved, const int32_t* list, const unsigned long long* list_count,
+                             unsigned long long* counter, cudaStream_t s) {
   if constexpr (PREC != MPT_FP64_PLAIN) {
     if (sch != nullptr && ((sch->warp_orders >> (N - 1)) & 1) != 0) {
       if (curved)

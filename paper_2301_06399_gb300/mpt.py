@@ -69,7 +69,8 @@ _lock = threading.Lock()
 SYMBOLS = ["mpt_ctx_create", "mpt_ctx_destroy", "mpt_ctx_sm_count", "mpt_ctx_check", "mpt_scene_upload",
            "mpt_scene_free", "mpt_enumerate", "mpt_candidate_count", "mpt_solve", "mpt_validate", "mpt_grad",
            "mpt_status_string", "mpt_flop_model", "mpt_validate_noalloc", "mpt_visibility", "mpt_field",
-           "mpt_ctx_selftest_wait", "mpt_image_method", "mpt_autotune", "mpt_scene_shift_planes"]
+           "mpt_ctx_selftest_wait", "mpt_image_method", "mpt_autotune", "mpt_scene_shift_planes",
+           "mpt_ctx_time_solver", "mpt_ctx_solver_ms"]
 
 
 def library_path() -> str:
@@ -90,6 +91,8 @@ def lib():
             L.mpt_ctx_sm_count.argtypes = [P]
             L.mpt_ctx_check.argtypes = [P, P]
             L.mpt_ctx_selftest_wait.argtypes = [P, P]
+            L.mpt_ctx_time_solver.argtypes = [P, C.c_int]
+            L.mpt_ctx_solver_ms.argtypes = [P, C.c_int, C.POINTER(C.c_float)]
             L.mpt_scene_upload.argtypes = [P, C.POINTER(SceneDesc), C.POINTER(P)]
             L.mpt_scene_free.argtypes = [P]
             L.mpt_enumerate.argtypes = [P, P, C.POINTER(Endpoints), C.c_int, P, C.POINTER(Sampling),
@@ -162,6 +165,16 @@ class Context:
 
     def check(self, stream=None) -> int:
         return int(lib().mpt_ctx_check(self.h, _stream(stream)))
+
+    def time_solver(self, on: bool) -> None:
+        """mpt_ctx_time_solver: record events around each order's solver launch."""
+        _check(lib().mpt_ctx_time_solver(self.h, 1 if on else 0), "mpt_ctx_time_solver")
+
+    def solver_ms(self, order: int) -> float:
+        """mpt_ctx_solver_ms: milliseconds of the last timed solver launch of `order`."""
+        ms = C.c_float()
+        _check(lib().mpt_ctx_solver_ms(self.h, order, C.byref(ms)), "mpt_ctx_solver_ms")
+        return float(ms.value)
 
     def selftest_wait(self, stream=None) -> int:
         """Enqueue the bounded-wait self-test (mpt_ctx_selftest_wait)."""

@@ -718,3 +718,25 @@ def test_device_plane_shift_equals_host_shift(mpt, ctx, which):
         m = r1.paths.n()
         assert m == r2.paths.n() > 100
         assert torch.equal(r1.paths.cand[:m], r2.paths.cand[:m]) and torch.equal(r1.paths.X[:, :m], r2.paths.X[:, :m])
+
+
+def test_solver_timing_events(mpt, ctx):
+    """mpt_ctx_time_solver / mpt_ctx_solver_ms: with timing on, the order-2
+    solver launch of the urban block (8x8 RX) has a positive duration and the
+    solutions are bit-identical to a solve with timing off."""
+    sc = S.urban_block(8)
+    spec = S.CONFIG_SPECS["urban_block"]
+    ds = mpt.DeviceScene(ctx, sc)
+    cands = mpt.enumerate_candidates(ds, 2, spec)
+    s_off = mpt.solve(ds, cands, mpt.FP32_FP64REFINE)
+    ctx.time_solver(True)
+    try:
+        s_on = mpt.solve(ds, cands, mpt.FP32_FP64REFINE)
+        torch.cuda.synchronize()
+        ms = ctx.solver_ms(2)
+    finally:
+        ctx.time_solver(False)
+    assert 0.0 < ms < 1000.0
+    assert torch.equal(s_on.T.view(torch.int64), s_off.T.view(torch.int64))
+    assert torch.equal(s_on.status, s_off.status)
+    print(f"order-2 solver launch: {ms:.3f} ms")
