@@ -18,7 +18,7 @@ arrays: the scene resident (uploaded once, like a model's weights), every
 step's TX/RX endpoints copied host->device and its valid paths (count,
 candidate ids, points, lengths) and TX gradient read device->host inside the
 timed region, steps pipelined over two contexts and streams.  The default
-800 steps keep the timed region above a second.  `workloads` times the other
+1000 steps keep the timed region above a second.  `workloads` times the other
 workloads as their own steps, outside the timed region: the street canyon
 (plain FP64 method and FP32 + refinement), the mixed-order city (library
 defaults and autotuned, eager and as a CUDA graph), the curved scene, the
@@ -790,7 +790,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=800)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
