@@ -344,7 +344,8 @@ __device__ __forceinline__ bool outside_beam(const float4* b, const float4 (&X)[
 // half-space or the beam condition rules b out.  A lane holds one object b
 // (its distinct vertices in registers) and a warp one word of 32 objects;
 // the warp walks a range of (e, a) pairs, whose beam faces are the same for
-// every lane (broadcast loads that do not depend on one another).
+// every lane: the range's beams (contiguous) are first copied to shared
+// memory by the whole warp, so that no iteration waits on an L2 read.
 constexpr int XBITS_PAIRS = 64;  // (e, a) pairs a warp walks
 
 __global__ void __launch_bounds__(128) k_exclusion_bits(DevScene sc, const float4* beams, int n_ends, int words,
@@ -357,6 +358,12 @@ __global__ void __launch_bounds__(128) k_exclusion_bits(DevScene sc, const float
   const int64_t q0 = (gw / words) * XBITS_PAIRS;         // the first (e, a) pair
   if (q0 >= total) return;                               // warp-uniform
   const int b = w * 32 + lane;
+  __shared__ float4 sbeam[4][XBITS_PAIRS * BEAM_F4];
+  float4* sb = sbeam[(threadIdx.x >> 5) & 3];
+  const int64_t q1 = q0 + XBITS_PAIRS < total ? q0 + XBITS_PAIRS : total;
+  const int nq = (int)(q1 - q0);
+  for (int i = lane; i < nq * BEAM_F4; i += 32) sb[i] = __ldg(beams + q0 * BEAM_F4 + i);
+  __syncwarp();
   float4 V[8];
   int nv = 0;
   if (b < no) {
@@ -368,18 +375,17 @@ __global__ void __launch_bounds__(128) k_exclusion_bits(DevScene sc, const float
     for (int k = 0; k < 8; ++k) V[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   int a = (int)(q0 % no);
-  const int64_t q1 = q0 + XBITS_PAIRS < total ? q0 + XBITS_PAIRS : total;
   for (int64_t q = q0; q < q1; ++q) {
     bool ex = false;
     if (__ldg(sc.kind + a) == K_PLANE && b < no && b != a) {
-      const float4* bm = beams + q * BEAM_F4;
-      const float h = __ldg(&bm->w);
+      const float4* bm = sb + (q - q0) * BEAM_F4;
+      const float h = bm->w;
       const int cls = __ldg(sc.side + (int64_t)a * no + b);
       ex = (h > m_end && cls < 0) || (h < -m_end && cls > 0);
       if (fabsf(h) > h_min) {
 #pragma unroll
         for (int f = 1; f <= 4; ++f) {
-          const float4 fq = __ldg(bm + f);
+          const float4 fq = bm[f];
           bool all = true;
 #pragma unroll
           for (int k = 0; k < 8; ++k)
