@@ -324,9 +324,10 @@ int64_t mpt_candidate_count(const mpt_scene* scene, const mpt_endpoints* ends, i
  * points inside their objects' bounds such a candidate's cost stays above
  * ~1e-11, far above any acceptance threshold: the exclusion removes no path.
  * The object-side and vertex tables are built at mpt_scene_upload (scenes of
- * at most 4096 objects; larger scenes, or more than 65535 endpoints, iterate
- * every candidate); the pass uses context scratch of 4 bytes per candidate
- * and 80 bytes per (endpoint, object). */
+ * at most 4096 objects); the pass uses context scratch of 4 bytes per
+ * candidate and 80 + n_obj / 8 bytes per (endpoint, object), grown on
+ * demand.  Scenes of more objects, more than 65535 endpoints, or exclusion
+ * bits beyond 256 MB iterate every candidate. */
 int mpt_solve(mpt_ctx* ctx, const mpt_scene* scene, const mpt_endpoints* ends,
               const mpt_candidates* cand, int precision, const mpt_schedule* schedule,
               mpt_solutions* out, void* stream);
