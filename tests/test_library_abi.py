@@ -91,3 +91,6 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.mpt_grad(None, None, None, None, None, None, None, None, None, None, None, None) == 1
     assert lib.mpt_enumerate(None, None, None, 2, None, None, None, None) == 1
     assert lib.mpt_ctx_destroy(None) == 1
+    assert lib.mpt_ctx_time_solver(None, 1) == 1
+    ms = C.c_float()
+    assert lib.mpt_ctx_solver_ms(None, 2, C.byref(ms)) == 1
