@@ -346,7 +346,7 @@ __device__ __forceinline__ bool outside_beam(const float4* b, const float4 (&X)[
 // the warp walks a range of (e, a) pairs, whose beam faces are the same for
 // every lane: the range's beams (contiguous) are first copied to shared
 // memory by the whole warp, so that no iteration waits on an L2 read.
-constexpr int XBITS_PAIRS = 64;  // (e, a) pairs a warp walks
+constexpr int XBITS_PAIRS = 16;  // (e, a) pairs a warp walks (enough warps per SM to hide the staging)
 
 __global__ void __launch_bounds__(128) k_exclusion_bits(DevScene sc, const float4* beams, int n_ends, int words,
                                                         uint32_t* xbits, float m_end, float m_beam, float h_min) {
