@@ -97,3 +97,32 @@ def test_single_reflection_across_a_plane_is_excluded_and_has_no_path():
     assert len(wall) == 1
     assert ex[wall[0]] and not ver.valid[wall[0]]
     assert not np.isfinite(sol.cost[wall[0]]) or sol.cost[wall[0]] > 1e-6
+
+
+@pytest.mark.parametrize("x_rx,expect_path", [(40.0, True), (80.0, False)])
+def test_beam_condition_on_a_single_wall_agrees_with_the_image_method(x_rx, expect_path):
+    """Street canyon, order 1, the wall y = +10 (x in [-50, 50]): TX (0, -5,
+    10) and RX (x_rx, 5, 10), both on its inner side.  The image method
+    (Eqs. 5-6) puts the reflection point where the segment from TX's image
+    (0, 25, 10) to RX crosses y = 10: x = 0.75 x_rx, 30 m for RX at 40 m
+    (inside the wall: a path) and 60 m for RX at 80 m (outside: no path).
+    The half-space test keeps both (same side); the beam test excludes
+    exactly the second, as the image method and the oracle decide."""
+    sc = S.street_canyon()
+    sc.tx = np.array([[0.0, -5.0, 10.0]])
+    sc.rx = np.array([[x_rx, 5.0, 10.0]])
+    sc = sc.contiguous()
+    table = oracle.enumerate_sequences(sc, 1, S.SequenceSpec(quota=(-1, 0, 0, 0)))
+    ex = F.exclusion_mask(sc, table)
+    half = F.exclusion_mask(sc, table, beam=False)
+    sol, ver = oracle.candidate_range(sc, table, 0, len(table) * sc.n_pairs)
+    wall = [e for e in range(len(table))
+            if abs(abs(sc.obj_param[int(table.ids[e][0])][1]) - 1.0) < 1e-12
+            and sc.obj_param[int(table.ids[e][0])][5] == 10.0]
+    assert len(wall) == 1
+    e = wall[0]
+    crossing = 0.75 * x_rx  # the image-method reflection point's x
+    assert (abs(crossing) <= 50.0) == expect_path
+    assert not half[e]
+    assert bool(ex[e]) == (not expect_path)
+    assert bool(ver.valid[e]) == expect_path
