@@ -107,6 +107,27 @@ def test_curved_root_sets_at_full_size(mpt, ctx, warp_orders):
     assert not diffs
 
 
+def test_curved_root_sets_plain_fp64(mpt, ctx):
+    """The curved workload with the plain FP64 GPU method (FP64 throughout,
+    the same starts): for every (pair, sequence) the sets of distinct valid
+    roots equal the oracle's, and the FP64 point error against the oracle is
+    reported beside the FP32-only and FP32 + refinement errors of the test
+    above."""
+    sc = S.curved_scene(n_pairs=4096)
+    spec = S.CONFIG_SPECS["curved"]
+    ds = mpt.DeviceScene(ctx, sc)
+    cands, sols, paths = _trace(mpt, ds, 3, spec, mpt.FP64_PLAIN)
+    table = oracle.enumerate_sequences(sc, 3, spec)
+    gpu = F.gpu_side(paths, sols)
+    rep = F.compare_workload(sc, table, gpu, keep_sets=True)
+    n_groups, diffs = F.root_set_differences(sc, table, gpu, rep)
+    print(f"\nPER-CONFIG curved_4096pairs_order3_fp64_plain: {rep.summary()}; root-set groups {n_groups}, "
+          f"differing {len(diffs)}")
+    for d in diffs[:20]:
+        print("  root-set difference:", d)
+    assert not diffs
+
+
 def test_differentiable_block_every_candidate_and_adjoint(mpt, ctx):
     """The urban block with 64x64 RX (38,539,264 candidates): valid set
     against the oracle, then the adjoint of the valid paths (length and point
