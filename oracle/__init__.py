@@ -7,7 +7,9 @@ FP64 C++, see its header for the paper passages each part follows); this
 module only compiles it with g++ and marshals numpy arrays.
 
 Parity unpinned: completeness of the multi-root solution sets of curved
-sequences of order >= 2 (multi-start agreement only).
+sequences of order 3 and of order-2 sequences with an arc edge
+(multi-start agreement only); orders 1 and 2 on paraboloids are pinned by
+dense scans of the path length's stationary points.
 """
 from __future__ import annotations
 

@@ -55,7 +55,9 @@
 //                  minimum length, 1e-6 m of a bound or of an occluder's
 //                  boundary) are flagged, not compared
 // Parity unpinned: completeness of multi-root solution sets for curved
-// sequences of order >= 2 (only multi-start agreement is available).
+// sequences of order 3 and for order-2 sequences with an arc edge (only
+// multi-start agreement is available); orders 1 and 2 on paraboloids are
+// pinned by dense scans of the path length's stationary points.
 #include <algorithm>
 #include <atomic>
 #include <cmath>

@@ -1,0 +1,156 @@
+"""Completeness of the oracle's root sets for curved sequences of order 2.
+
+Sec. III-B: where a curved object makes a sequence have several paths, the
+minimiser is started from several initial guesses, and every distinct root
+found is a path.  The order-1 pins check this against a dense scan of one
+surface; here the independent route covers order 2: two concave paraboloid
+mirrors facing each other (a deep bowl and an inverted one above it), TX and
+RX between them, and the sequences bowl -> upper mirror and back.  By
+Fermat's principle every path is a stationary point of the path length
+L = |X1 - TX| + |X2 - X1| + |RX - X2| over the four surface parameters; a
+damped Newton iteration on the gradient of L from a dense grid of starts on
+both discs (the Hessian by central differences) finds them, and those that
+obey the reflection law (Eq. 8) at both points inside both discs are the
+reference root set.  No occluders: the oracle's valid set is then the law,
+the bounds and the minimum segment.  Bar: with the 8 starts of the
+workloads every oracle root is in the reference set (no false root); with
+64 starts the two sets are equal.  Points within 1 mm of a rim are left out
+on both sides (the bounds band).
+"""
+import math
+
+import numpy as np
+
+import oracle
+from paper_2301_06399_gb300 import scenes as S
+
+BAND = 1e-3  # metres from a bound
+
+
+def _mirrors(rng):
+    """A deep bowl and a second paraboloid above it, inverted (two concave
+    mirrors facing each other), TX and RX between them."""
+    R = S._random_rotation(rng)
+    t0 = rng.uniform(-3, 3, 3)
+    h = rng.uniform(1.6, 2.6)
+    flip = np.diag([1.0, -1.0, -1.0])
+    bowl = dict(R=R, t0=t0, f=rng.uniform(0.5, 1.2), rho=2.0)
+    lid = dict(R=R @ flip, t0=t0 + R @ np.array([0.0, 0.0, h]), f=rng.uniform(0.5, 1.2), rho=2.0)
+    A = t0 + R @ np.array([*rng.uniform(-1.0, 1.0, 2), rng.uniform(0.4, h - 0.4)])
+    B = t0 + R @ np.array([*rng.uniform(-1.0, 1.0, 2), rng.uniform(0.4, h - 0.4)])
+    return dict(objs=(bowl, lid), A=A, B=B)
+
+
+def _surface(o, P):
+    s, t = P[:, 0], P[:, 1]
+    X = np.stack([s, t, (s * s + t * t) / (4 * o["f"])], 1) @ o["R"].T + o["t0"]
+    T0 = np.stack([np.ones_like(s), np.zeros_like(s), s / (2 * o["f"])], 1) @ o["R"].T
+    T1 = np.stack([np.zeros_like(s), np.ones_like(s), t / (2 * o["f"])], 1) @ o["R"].T
+    return X, (T0, T1)
+
+
+def _grad(g, P, seq):
+    (X1, T1), (X2, T2) = _surface(g["objs"][seq[0]], P[:, 0:2]), _surface(g["objs"][seq[1]], P[:, 2:4])
+    unit = lambda d: d / np.linalg.norm(d, axis=1, keepdims=True)
+    u0, u1, u2 = unit(X1 - g["A"]), unit(X2 - X1), unit(g["B"] - X2)
+    w1, w2 = u0 - u1, u1 - u2
+    return np.stack([(w1 * T1[0]).sum(1), (w1 * T1[1]).sum(1), (w2 * T2[0]).sum(1), (w2 * T2[1]).sum(1)], 1)
+
+
+def _normal(o, X):
+    loc = o["R"].T @ (X - o["t0"])
+    n = o["R"] @ np.array([loc[0] / (2 * o["f"]), loc[1] / (2 * o["f"]), -1.0])
+    return n / np.linalg.norm(n)
+
+
+def _obeys_law(g, X1, X2, seq, tol=1e-8):
+    pts = [g["A"], X1, X2, g["B"]]
+    for k in (1, 2):
+        i = (pts[k] - pts[k - 1]) / np.linalg.norm(pts[k] - pts[k - 1])
+        r = (pts[k + 1] - pts[k]) / np.linalg.norm(pts[k + 1] - pts[k])
+        n = _normal(g["objs"][seq[k - 1]], pts[k])
+        if np.linalg.norm(r - (i - 2 * np.dot(i, n) * n)) > tol:
+            return False
+    return True
+
+
+def _in_band(o, X):
+    loc = o["R"].T @ (X - o["t0"])
+    return math.hypot(loc[0], loc[1]) > o["rho"] - BAND
+
+
+def _reference_roots(g, seq, n=10):
+    """Stationary points of L from a dense grid of starts on both discs,
+    kept when both points obey Eq. 8 inside their discs by more than BAND."""
+    rho = 2.0
+    gd = np.linspace(-rho, rho, n)
+    D = np.stack(np.meshgrid(gd, gd, indexing="ij"), -1).reshape(-1, 2)
+    D = D[(D ** 2).sum(1) <= rho * rho]
+    P = np.concatenate([np.repeat(D, len(D), 0), np.tile(D, (len(D), 1))], 1)
+    h = 1e-7
+    for _ in range(60):
+        G = _grad(g, P, seq)
+        H = np.stack([(_grad(g, P + h * e, seq) - _grad(g, P - h * e, seq)) / (2 * h) for e in np.eye(4)], 2)
+        HtH = np.einsum("nki,nkj->nij", H, H) + 1e-14 * np.eye(4)
+        step = np.linalg.solve(HtH, np.einsum("nki,nk->ni", H, G)[..., None])[..., 0]
+        nrm = np.linalg.norm(step, axis=1, keepdims=True)
+        P = np.clip(P - step * np.minimum(1.0, 0.5 / np.maximum(nrm, 1e-300)), -6.0, 6.0)
+    P = P[np.linalg.norm(_grad(g, P, seq), axis=1) < 1e-10]
+    roots = []
+    for p in P:
+        if math.hypot(*p[0:2]) > rho - BAND or math.hypot(*p[2:4]) > rho - BAND:
+            continue
+        (X1, _), (X2, _) = _surface(g["objs"][seq[0]], p[None, 0:2]), _surface(g["objs"][seq[1]], p[None, 2:4])
+        if not _obeys_law(g, X1[0], X2[0], seq):
+            continue
+        x = np.concatenate([X1[0], X2[0]])
+        if not any(np.linalg.norm(x - q) < 1e-6 for q in roots):
+            roots.append(x)
+    return roots
+
+
+def _same(a, b, tol=1e-6):
+    missed = [x for x in a if not any(np.linalg.norm(x - q) < tol for q in b)]
+    extra = [x for x in b if not any(np.linalg.norm(x - q) < tol for q in a)]
+    return missed, extra
+
+
+def test_facing_mirrors_order2_root_sets_match_dense_scan():
+    rng = np.random.default_rng(7)
+    totals = {8: 0, 64: 0}
+    n_roots = n_multi = 0
+    for _ in range(24):
+        g = _mirrors(rng)
+        b = S._Builder()
+        for o in g["objs"]:
+            b.paraboloid(o["R"], o["t0"], o["f"], o["rho"], occluder=False)
+        sc = b.build("facing_mirrors", 100.0, g["A"][None], g["B"][None], pair_mode=1)
+        ref = {}
+        for seq in ((0, 1), (1, 0)):
+            ref[seq] = _reference_roots(g, seq)
+            n_roots += len(ref[seq])
+            n_multi += len(ref[seq]) > 1
+        for starts in (8, 64):
+            spec = S.SequenceSpec(quota=(0, -1, 0, 0), starts_curved=starts)
+            table = oracle.enumerate_sequences(sc, 2, spec)
+            sol, ver = oracle.candidate_range(sc, table, 0, len(table))
+            found = {(0, 1): [], (1, 0): []}
+            for c in range(len(table)):
+                if not ver.valid[c]:
+                    continue
+                seq = (int(table.ids[c][0]), int(table.ids[c][1]))
+                X1, X2 = sol.X[c, 0:3], sol.X[c, 3:6]
+                if _in_band(g["objs"][seq[0]], X1) or _in_band(g["objs"][seq[1]], X2):
+                    continue
+                x = np.concatenate([X1, X2])
+                if not any(np.linalg.norm(x - q) < 1e-6 for q in found[seq]):
+                    found[seq].append(x)
+            for seq in ((0, 1), (1, 0)):
+                missed, extra = _same(ref[seq], found[seq])
+                assert not extra, ("an oracle root that is not a reflection path", starts, seq)
+                if starts == 64:
+                    assert not missed, (len(missed), "roots missed with 64 starts", seq)
+                totals[starts] += len(ref[seq]) - len(missed)
+    print(f"facing mirrors, order 2: {n_roots} roots ({n_multi} sequences with several); "
+          f"found with 8 starts {totals[8]}, with 64 starts {totals[64]}")
+    assert n_roots >= 30 and n_multi >= 4
