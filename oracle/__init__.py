@@ -7,9 +7,11 @@ FP64 C++, see its header for the paper passages each part follows); this
 module only compiles it with g++ and marshals numpy arrays.
 
 Parity unpinned: completeness of the multi-root solution sets of curved
-sequences of order 3 and of order-2 sequences with an arc edge
-(multi-start agreement only); orders 1 and 2 on paraboloids are pinned by
-dense scans of the path length's stationary points.
+sequences of order 3 and of order-2 sequences that pair a curved object
+with a plane or straight edge, or two arc edges (multi-start agreement
+only); order 1, order 2 on two paraboloids and order 2 on an arc edge with
+a paraboloid are pinned by dense scans of the path length's stationary
+points.
 """
 from __future__ import annotations
 

@@ -55,9 +55,11 @@
 //                  minimum length, 1e-6 m of a bound or of an occluder's
 //                  boundary) are flagged, not compared
 // Parity unpinned: completeness of multi-root solution sets for curved
-// sequences of order 3 and for order-2 sequences with an arc edge (only
-// multi-start agreement is available); orders 1 and 2 on paraboloids are
-// pinned by dense scans of the path length's stationary points.
+// sequences of order 3 and for order-2 sequences that pair a curved object
+// with a plane or straight edge, or two arc edges (only multi-start
+// agreement is available); order 1, order 2 on two paraboloids and order 2
+// on an arc edge with a paraboloid are pinned by dense scans of the path
+// length's stationary points.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
