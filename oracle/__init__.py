@@ -6,12 +6,11 @@ binding never touch it.  The arithmetic lives in ``mpt_oracle.cpp`` (plain
 FP64 C++, see its header for the paper passages each part follows); this
 module only compiles it with g++ and marshals numpy arrays.
 
-Parity unpinned: completeness of the multi-root solution sets of curved
-sequences of order 3 and of order-2 sequences that pair a curved object
-with a plane or straight edge, or two arc edges (multi-start agreement
-only); order 1, order 2 on two paraboloids and order 2 on an arc edge with
-a paraboloid are pinned by dense scans of the path length's stationary
-points.
+Parity unpinned: completeness of the multi-root solution sets of order-3
+curved sequences beyond one three-object family, and of order 4
+(multi-start agreement only); curved sequences of every object kind at
+orders 1 and 2, and order 3 on a bowl, an arc and a plane, are pinned by
+dense scans of the path length's stationary points.
 """
 from __future__ import annotations
 

@@ -54,12 +54,11 @@
 //                  factor 100 of tau, a segment within a factor 3 of the
 //                  minimum length, 1e-6 m of a bound or of an occluder's
 //                  boundary) are flagged, not compared
-// Parity unpinned: completeness of multi-root solution sets for curved
-// sequences of order 3 and for order-2 sequences that pair a curved object
-// with a plane or straight edge, or two arc edges (only multi-start
-// agreement is available); order 1, order 2 on two paraboloids and order 2
-// on an arc edge with a paraboloid are pinned by dense scans of the path
-// length's stationary points.
+// Parity unpinned: completeness of multi-root solution sets for order-3
+// curved sequences beyond one three-object family, and for order 4 (only
+// multi-start agreement is available); curved sequences of every object
+// kind at orders 1 and 2, and order 3 on a bowl, an arc and a plane, are
+// pinned by dense scans of the path length's stationary points.
 #include <algorithm>
 #include <atomic>
 #include <cmath>

@@ -9,7 +9,7 @@ RX between them, and the sequences bowl -> upper mirror and back.  By
 Fermat's principle every path is a stationary point of the path length
 L = |X1 - TX| + |X2 - X1| + |RX - X2| over the four surface parameters; a
 damped Newton iteration on the gradient of L from a dense grid of starts on
-both discs (the Hessian by central differences) finds them, and those that
+both discs (the Hessian by forward differences) finds them, and those that
 obey the reflection law (Eq. 8) at both points inside both discs are the
 reference root set.  No occluders: the oracle's valid set is then the law,
 the bounds and the minimum segment.  Bar: with the 8 starts of the
@@ -91,12 +91,13 @@ def _reference_roots(g, seq, n=10):
     h = 1e-7
     for _ in range(60):
         G = _grad(g, P, seq)
-        H = np.stack([(_grad(g, P + h * e, seq) - _grad(g, P - h * e, seq)) / (2 * h) for e in np.eye(4)], 2)
+        H = np.stack([(_grad(g, P + h * e, seq) - G) / h for e in np.eye(4)], 2)
         HtH = np.einsum("nki,nkj->nij", H, H) + 1e-14 * np.eye(4)
         step = np.linalg.solve(HtH, np.einsum("nki,nk->ni", H, G)[..., None])[..., 0]
         nrm = np.linalg.norm(step, axis=1, keepdims=True)
         P = np.clip(P - step * np.minimum(1.0, 0.5 / np.maximum(nrm, 1e-300)), -6.0, 6.0)
     P = P[np.linalg.norm(_grad(g, P, seq), axis=1) < 1e-10]
+    P = P[np.unique(np.round(P, 7), axis=0, return_index=True)[1]]  # starts that reached one point
     roots = []
     for p in P:
         if math.hypot(*p[0:2]) > rho - BAND or math.hypot(*p[2:4]) > rho - BAND:
@@ -206,13 +207,14 @@ def _arc_bowl_roots(g, n_phi=24, n=9):
     h = 1e-7
     for _ in range(60):
         G = _grad_arc_bowl(g, P)
-        H = np.stack([(_grad_arc_bowl(g, P + h * e) - _grad_arc_bowl(g, P - h * e)) / (2 * h) for e in np.eye(3)], 2)
+        H = np.stack([(_grad_arc_bowl(g, P + h * e) - G) / h for e in np.eye(3)], 2)
         HtH = np.einsum("nki,nkj->nij", H, H) + 1e-14 * np.eye(3)
         step = np.linalg.solve(HtH, np.einsum("nki,nk->ni", H, G)[..., None])[..., 0]
         nrm = np.linalg.norm(step, axis=1, keepdims=True)
         P = P - step * np.minimum(1.0, 0.5 / np.maximum(nrm, 1e-300))
         P[:, 1:3] = np.clip(P[:, 1:3], -6.0, 6.0)
     P = P[np.linalg.norm(_grad_arc_bowl(g, P), axis=1) < 1e-10]
+    P = P[np.unique(np.round(P, 7), axis=0, return_index=True)[1]]  # starts that reached one point
     roots = []
     for p in P:
         if not _arc_in_range(arc, p[0], BAND) or math.hypot(p[1], p[2]) > 2.0 - BAND:
