@@ -6,11 +6,12 @@ binding never touch it.  The arithmetic lives in ``mpt_oracle.cpp`` (plain
 FP64 C++, see its header for the paper passages each part follows); this
 module only compiles it with g++ and marshals numpy arrays.
 
-Parity unpinned: completeness of the multi-root solution sets of order-3
-curved sequences beyond one three-object family, and of order 4
-(multi-start agreement only); curved sequences of every object kind at
-orders 1 and 2, and order 3 on a bowl, an arc and a plane, are pinned by
-dense scans of the path length's stationary points.
+Completeness of the multi-root solution sets is pinned by dense scans of
+the path length's stationary points: curved sequences of every object
+kind at orders 1 and 2, and at order 3 two three-object families in all
+six orders (every kind in every position); other order-3 combinations run
+the same per-interaction code and are compared by multi-start agreement
+only.
 """
 from __future__ import annotations
 

@@ -54,11 +54,12 @@
 //                  factor 100 of tau, a segment within a factor 3 of the
 //                  minimum length, 1e-6 m of a bound or of an occluder's
 //                  boundary) are flagged, not compared
-// Parity unpinned: completeness of multi-root solution sets for order-3
-// curved sequences beyond one three-object family, and for order 4 (only
-// multi-start agreement is available); curved sequences of every object
-// kind at orders 1 and 2, and order 3 on a bowl, an arc and a plane, are
-// pinned by dense scans of the path length's stationary points.
+// Completeness of multi-root solution sets is pinned by dense scans of
+// the path length's stationary points: curved sequences of every object
+// kind at orders 1 and 2, and at order 3 two three-object families in all
+// six orders (every kind in every position); other order-3 combinations
+// run the same per-interaction code and are compared by multi-start
+// agreement only.
 #include <algorithm>
 #include <atomic>
 #include <cmath>

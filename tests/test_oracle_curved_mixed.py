@@ -340,6 +340,24 @@ def bowl_rim_and_lid(rng):
     return [bowl, rim, lid], A, B
 
 
+def bowl_edge_and_lid(rng):
+    """Order 3 with a straight edge: a deep bowl, a 6 m straight edge 0.3-0.8 m
+    above the bowl's surface where it crosses the axis (within 0.8 m of it)
+    and a flat 5 m square lid 0.8-1.4 m above the edge."""
+    R, t0 = _frame(rng)
+    f = rng.uniform(0.5, 1.2)
+    bowl = _bowl(R, t0, f)
+    a = rng.uniform(0, 2 * math.pi)
+    e = R @ np.array([math.cos(a), math.sin(a), 0.0])
+    off = rng.uniform(-0.8, 0.8, 2)
+    z_edge = float(off @ off) / (4 * f) + rng.uniform(0.3, 0.8)
+    h = z_edge + rng.uniform(0.8, 1.4)
+    lid = _plane(t0 + R @ np.array([-2.5, -2.5, h]), R[:, 0], R[:, 1], 5.0, 5.0)
+    edge = _line(t0 + R @ np.array([off[0], off[1], z_edge]), e, -3.0, 3.0)
+    A, B = _endpoints(rng, R, t0, 0.4, h - 0.4)
+    return [bowl, edge, lid], A, B
+
+
 def test_plane_with_paraboloid_order2():
     n, multi, found = _run(flat_lid_over_bowl, 30, 2, [(0, 1), (1, 0)], 8, (8, 64, 256), seed=21)
     assert n >= 40 and multi >= 3
@@ -364,3 +382,9 @@ def test_bowl_rim_and_lid_order3():
     seqs = [(0, 1, 2), (2, 1, 0), (1, 0, 2), (0, 2, 1), (2, 0, 1), (1, 2, 0)]
     n, multi, found = _run(bowl_rim_and_lid, 8, 3, seqs, 5, (8, 64, 1024), seed=24)
     assert n >= 40 and multi >= 6
+
+
+def test_bowl_edge_and_lid_order3():
+    seqs = [(0, 1, 2), (2, 1, 0), (1, 0, 2), (0, 2, 1), (2, 0, 1), (1, 2, 0)]
+    n, multi, found = _run(bowl_edge_and_lid, 6, 3, seqs, 5, (8, 64, 1024), seed=27)
+    assert n >= 25
