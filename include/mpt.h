@@ -145,7 +145,9 @@ typedef struct {
  * edge, in id order, of the r edges not taken yet (k = 0, 1); the remaining
  * positions then continue the draws from k = 2.  Sequences containing a
  * paraboloid or an arc are repeated `starts_curved` times with start index
- * 0..starts_curved-1. */
+ * 0..starts_curved-1.  starts_curved <= 0 means 1; the start index is held
+ * in 8 bits of the candidate record, so starts_curved > 255 makes
+ * mpt_enumerate return MPT_ERR_ARG and mpt_candidate_count return -1. */
 typedef struct {
   int64_t quota[MPT_MAX_ORDER];
   uint64_t seed;
