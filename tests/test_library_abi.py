@@ -94,3 +94,50 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.mpt_ctx_time_solver(None, 1) == 1
     ms = C.c_float()
     assert lib.mpt_ctx_solver_ms(None, 2, C.byref(ms)) == 1
+
+
+def _prototypes():
+    """name -> (return type, [argument types]) parsed from include/mpt.h."""
+    text = open(os.path.join(ROOT, "include", "mpt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for ret, name, args in re.findall(r"([A-Za-z_][\w \*]*?)\s*\b(mpt_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text):
+        parts = [a.strip() for a in args.replace("\n", " ").split(",") if a.strip() and a.strip() != "void"]
+        # drop the parameter name, keep the type (with any '*')
+        types = [re.sub(r"\b[A-Za-z_]\w*\s*$", "", a).strip() if not a.endswith("*") else a for a in parts]
+        out[name] = (ret.strip(), types)
+    return out
+
+
+def _kind_c(t: str) -> str:
+    if "*" in t:
+        return "ptr"
+    t = t.replace("const", "").strip()
+    return {"int": "i32", "int32_t": "i32", "int64_t": "i64", "uint64_t": "u64", "double": "f64",
+            "float": "f32"}[t]
+
+
+def _kind_ctypes(t) -> str:
+    if t in (C.c_void_p, C.c_char_p) or (isinstance(t, type) and issubclass(t, C._Pointer)):
+        return "ptr"
+    for k, ct in (("i32", C.c_int32), ("i64", C.c_int64), ("u64", C.c_uint64), ("f64", C.c_double),
+                  ("f32", C.c_float)):
+        if t is ct:
+            return k
+    raise AssertionError(t)
+
+
+def test_binding_signatures_match_the_header(lib):
+    protos = _prototypes()
+    from paper_2301_06399_gb300 import mpt
+
+    assert sorted(protos) == sorted(mpt.SYMBOLS)
+    for name, (ret, args) in protos.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == len(args), (name, len(fn.argtypes), args)
+        for i, (want, got) in enumerate(zip(args, fn.argtypes)):
+            assert _kind_c(want) == _kind_ctypes(got), (name, i, want, got)
+        want_ret = _kind_c(ret)
+        got_ret = "i32" if fn.restype is C.c_int else _kind_ctypes(fn.restype)
+        assert want_ret == got_ret, (name, ret, fn.restype)
