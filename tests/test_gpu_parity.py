@@ -142,6 +142,24 @@ def test_enumeration_capacity_error(mpt, ctx):
         mpt.enumerate_candidates(ds, 2, S.CONFIG_SPECS["street_canyon"], capacity=100)
 
 
+def test_start_count_limit(mpt, ctx):
+    """A candidate record holds the start index in 8 bits: 255 starts are
+    accepted, 256 are an argument error of both the count and the
+    enumeration, which enqueue nothing."""
+    sc = S.curved_scene(n_pairs=4)
+    ds = mpt.DeviceScene(ctx, sc)
+    ok = S.SequenceSpec(quota=(-1, 0, 0, 0), starts_curved=255)
+    n = mpt.candidate_count(ds, 1, ok)
+    n_curved = int(np.isin(sc.obj_kind, (S.PARABOLOID, S.ARC_EDGE)).sum())
+    assert n == ((sc.n_obj - n_curved) + 255 * n_curved) * sc.n_pairs
+    bad = S.SequenceSpec(quota=(-1, 0, 0, 0), starts_curved=256)
+    with pytest.raises(RuntimeError, match="bad arguments"):
+        mpt.candidate_count(ds, 1, bad)
+    with pytest.raises(RuntimeError, match="ARG"):
+        mpt.enumerate_candidates(ds, 1, bad, capacity=n)
+    assert ctx.check() == 0
+
+
 # ------------------------------------------------------------------ Fig. 4 --
 @pytest.mark.parametrize("prec", ["FP64_PLAIN", "FP32_FP64REFINE"])
 def test_fig4_gpu_path(mpt, ctx, prec):
