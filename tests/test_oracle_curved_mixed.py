@@ -358,6 +358,25 @@ def bowl_edge_and_lid(rng):
     return [bowl, edge, lid], A, B
 
 
+def three_mirrors(rng):
+    """Order 3 on three paraboloids: a deep bowl, an inverted paraboloid
+    1.8-2.6 m above it, and a shallow side mirror (focal length 3-5 m, disc
+    radius 1.5 m) 3 m from their axis at mid height, its axis pointing at
+    theirs; TX and RX between bowl and lid."""
+    R, t0 = _frame(rng)
+    h = rng.uniform(1.8, 2.6)
+    flip = np.diag([1.0, -1.0, -1.0])
+    bowl = _bowl(R, t0, rng.uniform(0.5, 1.2))
+    lid = _bowl(R @ flip, t0 + R @ np.array([0.0, 0.0, h]), rng.uniform(0.5, 1.2))
+    a = rng.uniform(0, 2 * math.pi)
+    d = np.array([math.cos(a), math.sin(a), 0.0])
+    up, axis = np.array([0.0, 0.0, 1.0]), -d
+    side = _bowl(R @ np.stack([up, np.cross(axis, up), axis], 1), t0 + R @ (3.0 * d + np.array([0.0, 0.0, h / 2])),
+                 rng.uniform(3.0, 5.0), rho=1.5)
+    A, B = _endpoints(rng, R, t0, 0.4, h - 0.4)
+    return [bowl, lid, side], A, B
+
+
 def test_plane_with_paraboloid_order2():
     n, multi, found = _run(flat_lid_over_bowl, 30, 2, [(0, 1), (1, 0)], 8, (8, 64, 256), seed=21)
     assert n >= 40 and multi >= 3
@@ -388,3 +407,9 @@ def test_bowl_edge_and_lid_order3():
     seqs = [(0, 1, 2), (2, 1, 0), (1, 0, 2), (0, 2, 1), (2, 0, 1), (1, 2, 0)]
     n, multi, found = _run(bowl_edge_and_lid, 6, 3, seqs, 5, (8, 64, 1024), seed=27)
     assert n >= 25
+
+
+def test_three_paraboloids_order3():
+    seqs = [(0, 1, 2), (2, 1, 0), (1, 0, 2), (0, 2, 1), (2, 0, 1), (1, 2, 0)]
+    n, multi, found = _run(three_mirrors, 12, 3, seqs, 4, (8, 64, 1024), seed=28)
+    assert n >= 20
