@@ -190,7 +190,9 @@ def _reference_roots(objs, A, B, n_grid):
     return roots
 
 
-def _oracle_roots(sc, objs, seq, order, starts, A, B):
+def _oracle_roots(sc, objs, order, starts, A, B):
+    """The oracle's distinct valid roots per sequence, with the same exclusions
+    as the reference."""
     q = [0, 0, 0, 0]
     q[order - 1] = -1
     spec = S.SequenceSpec(quota=tuple(q), starts_curved=starts)
@@ -250,7 +252,7 @@ def _run(family, n_inst, order, seqs, n_grid, start_levels, seed):
             n_roots += len(ref)
             n_multi += len(ref) > 1
         for starts in start_levels:
-            sets = _oracle_roots(sc, objs, seqs, order, starts, A, B)
+            sets = _oracle_roots(sc, objs, order, starts, A, B)
             for seq, ref in refs.items():
                 missed, extra = _same(ref, sets.get(seq, []))
                 assert not extra, ("an oracle root that is not a path", family.__name__, seq, starts, extra)
