@@ -8,7 +8,7 @@ module only compiles it with g++ and marshals numpy arrays.
 
 Completeness of the multi-root solution sets is pinned by dense scans of
 the path length's stationary points: curved sequences of every object
-kind at orders 1 and 2, and at order 3 three three-object families in all
+kind at orders 1 and 2, and at order 3 five three-object families in all
 six orders (every kind in every position); other order-3 combinations run
 the same per-interaction code and are compared by multi-start agreement
 only.

@@ -379,6 +379,33 @@ def three_mirrors(rng):
     return [bowl, lid, side], A, B
 
 
+def two_arcs_over_floor(rng):
+    """Order 3 with two edges and a plane: two arc edges around one vertical
+    axis, 0.8-1.2 m and 1.8-2.4 m above a 6 m square floor (radii 1-2 m,
+    120-270 degrees); TX and RX near the axis."""
+    R, t0 = _frame(rng)
+    floor = _plane(t0 + R @ np.array([-3.0, -3.0, 0.0]), R[:, 0], R[:, 1], 6.0, 6.0)
+    arcs = []
+    for z in (rng.uniform(0.8, 1.2), rng.uniform(1.8, 2.4)):
+        phi0 = rng.uniform(-math.pi, math.pi)
+        arcs.append(_arc(t0 + R @ np.array([0.0, 0.0, z]), R[:, 2], R[:, 0], rng.uniform(1.0, 2.0),
+                         phi0, phi0 + rng.uniform(2 * math.pi / 3, 1.5 * math.pi)))
+    A, B = _endpoints(rng, R, t0, 0.3, 2.8, r=0.8)
+    return [floor, *arcs], A, B
+
+
+def bowl_between_walls(rng):
+    """Order 3 with two planes and a paraboloid: a deep bowl between two
+    facing vertical walls (6 m by 4 m, 2.2-3 m from its axis on either
+    side); TX and RX above the bowl."""
+    R, t0 = _frame(rng)
+    bowl = _bowl(R, t0, rng.uniform(0.5, 1.2))
+    w = rng.uniform(2.2, 3.0, 2)
+    walls = [_plane(t0 + R @ np.array([x, -3.0, -0.5]), R[:, 1], R[:, 2], 6.0, 4.0) for x in (w[0], -w[1])]
+    A, B = _endpoints(rng, R, t0, 0.4, 2.5, r=1.5)
+    return [bowl, *walls], A, B
+
+
 def test_plane_with_paraboloid_order2():
     n, multi, found = _run(flat_lid_over_bowl, 30, 2, [(0, 1), (1, 0)], 8, (8, 64, 256), seed=21)
     assert n >= 40 and multi >= 3
@@ -415,3 +442,15 @@ def test_three_paraboloids_order3():
     seqs = [(0, 1, 2), (2, 1, 0), (1, 0, 2), (0, 2, 1), (2, 0, 1), (1, 2, 0)]
     n, multi, found = _run(three_mirrors, 12, 3, seqs, 4, (8, 64, 1024), seed=28)
     assert n >= 20
+
+
+def test_two_arcs_over_floor_order3():
+    seqs = [(0, 1, 2), (2, 1, 0), (1, 0, 2), (0, 2, 1), (2, 0, 1), (1, 2, 0)]
+    n, multi, found = _run(two_arcs_over_floor, 8, 3, seqs, 5, (8, 64, 1024), seed=29)
+    assert n >= 40 and multi >= 10
+
+
+def test_bowl_between_walls_order3():
+    seqs = [(0, 1, 2), (2, 1, 0), (1, 0, 2), (0, 2, 1), (2, 0, 1), (1, 2, 0)]
+    n, multi, found = _run(bowl_between_walls, 5, 3, seqs, 5, (8, 64, 1024), seed=30)
+    assert n >= 15
